@@ -1,0 +1,205 @@
+/*
+ * ddm.h -- C ABI of the GB300 (sm_103a) additive overlapping domain
+ * decomposition solver for the Helmholtz equation with PML
+ * (Leng & Ju, "An Additive Overlapping Domain Decomposition Method for the
+ * Helmholtz Equation", 2018).
+ *
+ * Problem (Sections 1, 2.1, 3.1):  Delta u + k^2 u = f, k(x) = omega / c(x),
+ * truncated by a uniaxial PML (alpha = 1 + i sigma) and discretised by the
+ * 5-point (2D) / 7-point (3D) finite-difference operator in its J-scaled,
+ * complex-symmetric form
+ *     (A u)(x) = sum_a prod_{b!=a} alpha_b [ (u(x+e_a)-u(x))/alpha_a(x_a+1/2)
+ *                                           - (u(x)-u(x-e_a))/alpha_a(x_a-1/2) ]
+ *                + h^2 k^2 prod_a alpha_a u(x),          A u = b = h^2 J f,
+ * with homogeneous Dirichlet values beyond the extended grid.
+ *
+ * Method (Algorithm 3.1): the interior is cut into N1 x N2 (x N3) boxes; each
+ * box plus an overlap of `overlap` cells and a PML of `pml` cells is a
+ * subdomain.  Step 1 solves every subdomain problem with its restricted
+ * source; step s >= 2 solves them with the directional residuals Psi of the
+ * neighbours (8 directions in 2D, 26 in 3D; faces lagged one step, corners
+ * two, 3D vertices three).  The DDM solution is sum beta_0 * sum_s u^s.
+ * The same steps form the preconditioner M_K of flexible GMRES (Section 4.2).
+ *
+ * Grid and memory layout
+ *   - Physical axis 0 is x (fastest varying), 1 is y, 2 is z.  Interior node p
+ *     sits at (p + 1/2) h; the global extended grid adds e = overlap + pml
+ *     nodes per side, so it has (n[a] + 2e) nodes along axis a.
+ *   - "Global vectors" are complex128 (interleaved re, im doubles) arrays over
+ *     the global extended grid, x fastest, then y, then z, one after another
+ *     for several right-hand sides (stride = number of global nodes).
+ *   - The wave speed `c` is a float64 array over the global extended grid.
+ *   - "Local vectors" (debug/parity entry points only) concatenate every
+ *     subdomain's extended grid (x fastest), subdomains in C order of their
+ *     index (z slowest, x fastest); ddm_local_layout() gives the offsets.
+ *
+ * Conventions for every entry point
+ *   - Returns a ddm_status; never aborts or exits.  On error the context keeps
+ *     a message, readable with ddm_last_error().
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller and
+ *     valid only during the call; *_host are host pointers.  The library never
+ *     frees caller memory.  Work is enqueued on the stream given at set-up;
+ *     entry points that return results to the host synchronise that stream.
+ *   - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef DDM_H
+#define DDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDM_OK = 0,
+  DDM_E_INVAL = 1,     /* bad argument or parameter combination            */
+  DDM_E_NOMEM = 2,     /* device allocation failed                          */
+  DDM_E_CUDA = 3,      /* a CUDA call or kernel launch failed               */
+  DDM_E_STATE = 4,     /* call out of order (e.g. solve before factor)      */
+  DDM_E_SINGULAR = 5,  /* a pivot of a subdomain factor was (near) zero     */
+  DDM_E_NOCONV = 6,    /* tolerance not reached within the iteration limit  */
+  DDM_E_TIMEOUT = 7,   /* a bounded device-side wait gave up                */
+  DDM_E_BUDGET = 8     /* request exceeds the configured memory budget      */
+} ddm_status;
+
+enum { DDM_FP64 = 0, DDM_MIXED = 1 };         /* precision of the local solves  */
+enum { DDM_STEPPING = 0, DDM_FGMRES = 1 };    /* solver mode of ddm_solve       */
+
+typedef struct ddm_ctx ddm_ctx;
+
+typedef struct {
+  int dim;                  /* 2 or 3                                                   */
+  int64_t n[3];             /* interior nodes per physical axis (x, y, z)               */
+  double h;                 /* uniform spacing                                          */
+  int parts[3];             /* N1, N2 (, N3): subdomains per axis (Section 2.2)         */
+  const int64_t *cuts[3];   /* host arrays of parts[a]+1 increasing node offsets from 0
+                               to n[a] (uneven partitions); NULL = uniform cuts         */
+  int overlap;              /* ov >= 1 cells: overlap width d~ = ov h (Eq. (PMLprofile))*/
+  int pml;                  /* PML cells beyond the overlap                             */
+  double sigma0;            /* PML profile sigma(t) = sigma0 ((t - ov)/pml)^pml_power   */
+  double pml_power;         /*   for t > ov cells beyond a box face, 0 otherwise        */
+  int precision;            /* DDM_FP64, or DDM_MIXED: complex64 factors, local solves
+                               and transfers inside complex128 Krylov / residuals       */
+  int max_rhs;              /* largest nrhs passed to ddm_apply / ddm_solve             */
+} ddm_params;
+
+typedef struct {
+  int iters;                /* FGMRES iterations (or DDM steps in stepping mode)        */
+  int ddm_steps;            /* DDM steps taken = local solves per subdomain             */
+  int converged;            /* 1 if rel_residual <= tol                                  */
+  int n_unique_factors;     /* distinct subdomain factors actually computed             */
+  double rel_residual;      /* explicit ||b - A u||_2 / ||b||_2 in FP64 at exit         */
+  double rel_residual_est;  /* last Krylov / strip-residual estimate                    */
+  double factor_ms;         /* device time of the last ddm_factor                       */
+  double solve_ms;          /* wall time of this ddm_solve call                         */
+} ddm_info;
+
+/* Set-up (Sections 2.1, 3.1; assembly step of the path).  Validates `p`,
+ * copies the wave speed c_dev (float64, global extended grid, device) and
+ * builds on the device the PML stretching tables (alpha = 1 + i sigma at nodes
+ * and half nodes, Eq. (PMLprofile)), k^2 = (omega / c)^2 and the partition
+ * descriptors.  Allocates all device workspace for up to p->max_rhs
+ * right-hand sides.  `stream` is a cudaStream_t (NULL = legacy default).
+ * Does not factor.  Errors: DDM_E_INVAL, DDM_E_NOMEM, DDM_E_CUDA.           */
+ddm_status ddm_setup(const ddm_params *p, double omega, const double *c_dev, void *stream, ddm_ctx **out);
+
+/* Factor every distinct subdomain operator (Algorithm 3.1's local problems;
+ * the paper uses a sparse direct solver).  Subdomains whose extended grids
+ * carry identical operators share one factor.  Each factor is the block
+ * tridiagonal LU in explicit-inverse form: G_k = D_k^{-1} with
+ * D_k = T_k - L_k G_{k-1} U_{k-1} over the x-lines (2D) of the subdomain,
+ * each D_k inverted by Gauss-Jordan with partial pivoting inside the block.
+ * Errors: DDM_E_SINGULAR if a pivot fell below 1e-30 relative to its column,
+ * DDM_E_CUDA, DDM_E_STATE.                                                  */
+ddm_status ddm_factor(ddm_ctx *ctx);
+
+/* dst = M_K(src): K steps of Algorithm 3.1 with right-hand side src, then the
+ * assembled DDM solution sum_R beta_{0;R} sum_s u^s_R (Eq. (tsum)).  src and
+ * dst are global complex128 vectors (nrhs of them, device).  src is in the
+ * J-scaled space of b.  Requires ddm_factor.  Errors: DDM_E_INVAL (K < 1,
+ * nrhs > max_rhs), DDM_E_STATE, DDM_E_CUDA.                                 */
+ddm_status ddm_apply(ddm_ctx *ctx, int K, const void *src_dev, void *dst_dev, int nrhs);
+
+/* Solve A u = h^2 J f for nrhs right-hand sides f (global complex128, device)
+ * into u (device).  mode DDM_FGMRES: flexible GMRES(restart) right-
+ * preconditioned by M_K, x0 = 0, classical Gram-Schmidt twice, stop when the
+ * least-squares residual estimate <= tol (Section 4.2.2).  mode DDM_STEPPING:
+ * Algorithm 3.1 continued as an iteration (Section 4.2.1), residual of the
+ * assembled solution from the transfers of the last steps; in DDM_MIXED it
+ * runs as iterative refinement around complex64 steps.  max_it bounds
+ * FGMRES iterations (or DDM steps).  Every exit is checked with an explicit
+ * FP64 residual, reported in info (may be NULL).  Errors: DDM_E_NOCONV,
+ * DDM_E_INVAL, DDM_E_STATE, DDM_E_CUDA.                                     */
+ddm_status ddm_solve(ddm_ctx *ctx, const void *f_dev, void *u_dev, int nrhs, double tol, int max_it,
+                     int mode, int K, int restart, ddm_info *info);
+
+/* ddm_solve with host buffers: copies f_host (complex128, nrhs global
+ * vectors) to the device, solves, copies u back to u_host, synchronising the
+ * stream.  Pinned host memory makes the copies asynchronous.                */
+ddm_status ddm_solve_host(ddm_ctx *ctx, const void *f_host, void *u_host, int nrhs, double tol, int max_it,
+                          int mode, int K, int restart, ddm_info *info);
+
+/* Release every device allocation of the context.  NULL is a no-op.        */
+ddm_status ddm_destroy(ddm_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed ddm_setup when
+ * ctx is NULL).  The string lives until the next call on the context.      */
+const char *ddm_last_error(const ddm_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks, exported for parity tests and measurement.  All operate
+ * on the context's partition and stream.
+ * ------------------------------------------------------------------------ */
+
+/* b = h^2 J f on the global grid (right-hand side of the J-scaled system,
+ * Eq. (PMLweak0)).  Global complex128 vectors, device.                      */
+ddm_status ddm_rhs(ddm_ctx *ctx, const void *f_dev, void *b_dev, int nrhs);
+
+/* y = A x with the global truncated operator (Section 3.1), FP64.          */
+ddm_status ddm_global_apply(ddm_ctx *ctx, const void *x_dev, void *y_dev, int nrhs);
+
+/* r = b - A x and, per right-hand side, norms_host[2*i] = ||r_i||_2,
+ * norms_host[2*i+1] = ||b_i||_2 (FP64; synchronises).                       */
+ddm_status ddm_residual(ddm_ctx *ctx, const void *b_dev, const void *x_dev, void *r_dev, int nrhs,
+                        double *norms_host);
+
+/* Local layout: number of subdomains, total local length, and (optional,
+ * host arrays of n_sub entries) each subdomain's element offset and its
+ * extended size along x, y, z.                                              */
+ddm_status ddm_local_layout(const ddm_ctx *ctx, int *n_sub, int64_t *total, int64_t *offsets,
+                            int *ext_x, int *ext_y, int *ext_z);
+
+/* u_R = L^_R^{-1} src_R for every subdomain R (the batched local solves of
+ * Eqs. (talg_1)/(talg_2)); local complex vectors, device, in the context's
+ * local precision (complex128 for DDM_FP64, complex64 for DDM_MIXED).      */
+ddm_status ddm_local_solve(ddm_ctx *ctx, const void *src_dev, void *u_dev, int nrhs);
+
+/* Run `nsteps` steps of Algorithm 3.1 from the global right-hand side b_dev
+ * (one right-hand side) and return: w_dev = the assembled solution after the
+ * last step (global complex128, device, may be NULL); u_last_dev = the last
+ * step's local solutions (local layout/precision, device, may be NULL); and
+ * res_host[s-1] = || sum of the directional residuals of steps s, s-1(, s-2)
+ * on the own regions ||_2 (= ||b - A w_s|| in exact arithmetic), s = 1..nsteps
+ * (host array of nsteps doubles, may be NULL; res_host[0] is computed from
+ * step 1's transfers).  Synchronises.                                       */
+ddm_status ddm_steps(ddm_ctx *ctx, const void *b_dev, int nsteps, void *w_dev, void *u_last_dev,
+                     double *res_host);
+
+/* Device time of the kernels launched since the last reset, accumulated with
+ * CUDA events on the context's stream when timing is enabled:
+ * out_ms[0] local solves, [1] transfers, [2] assembly/restriction,
+ * [3] global operator, [4] Krylov (Arnoldi, updates), [5] factorisation;
+ * out_launches[i] the matching launch counts (either array may be NULL).
+ * enable != 0 turns recording on, 0 off; reset clears the sums.            */
+ddm_status ddm_timing(ddm_ctx *ctx, int enable, int reset, double *out_ms, int64_t *out_launches);
+
+/* Bytes of subdomain factors read by one batched local solve of one
+ * right-hand side per subdomain (each distinct factor streamed twice, once
+ * per sweep, per subdomain using it), and bytes of factor storage.          */
+ddm_status ddm_factor_bytes(const ddm_ctx *ctx, int64_t *bytes_per_solve, int64_t *bytes_stored);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDM_H */

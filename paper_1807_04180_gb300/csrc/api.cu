@@ -1,0 +1,716 @@
+// C ABI of libddm: set-up, factorisation with sharing of identical subdomains, the DDM
+// step loop of Algorithm 3.1, the DDM(K) preconditioner, flexible GMRES and the stepping
+// solver of Section 4.2.  Host code only orchestrates; all arithmetic runs in the kernels.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ddm_internal.cuh"
+
+using namespace ddm;
+
+
+static std::string g_setup_err;
+
+static ddm_status fail(ddm_ctx* c, ddm_status st, const std::string& msg) {
+  if (c) c->err = msg; else g_setup_err = msg;
+  return st;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return fail(c, _e == cudaErrorMemoryAllocation ? DDM_E_NOMEM : DDM_E_CUDA,              \
+                  std::string(#call) + ": " + cudaGetErrorString(_e));                        \
+  } while (0)
+
+#define CKS(expr)                 \
+  do {                            \
+    ddm_status _s = (expr);       \
+    if (_s != DDM_OK) return _s;  \
+  } while (0)
+
+static size_t local_elem(const ddm_ctx* c) { return c->prec == DDM_MIXED ? sizeof(c32) : sizeof(z64); }
+
+// ------------------------------------------------------------------ timing helpers
+static cudaEvent_t ev_get(ddm_ctx* c) {
+  if (!c->ev_pool.empty()) { cudaEvent_t e = c->ev_pool.back(); c->ev_pool.pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+static void timing_drain(ddm_ctx* c) {
+  for (auto& pe : c->ev_pending) {
+    cudaEventSynchronize(pe.second.second);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pe.second.first, pe.second.second);
+    c->t_ms[pe.first] += ms;
+    c->t_n[pe.first] += 1;
+    c->ev_pool.push_back(pe.second.first);
+    c->ev_pool.push_back(pe.second.second);
+  }
+  c->ev_pending.clear();
+}
+struct TScope {
+  ddm_ctx* c; int slot; cudaEvent_t e0 = nullptr;
+  TScope(ddm_ctx* cc, int s) : c(cc), slot(s) {
+    if (c->timing) { e0 = ev_get(c); cudaEventRecord(e0, c->st); }
+  }
+  ~TScope() {
+    if (c->timing) {
+      cudaEvent_t e1 = ev_get(c);
+      cudaEventRecord(e1, c->st);
+      c->ev_pending.push_back({slot, {e0, e1}});
+      if (c->ev_pending.size() > 4096) timing_drain(c);
+    }
+  }
+};
+
+static ddm_status check_err_word(ddm_ctx* c) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (h & ERRBIT_TIMEOUT) return fail(c, DDM_E_TIMEOUT, "a bounded device wait timed out");
+  if (h & ERRBIT_SINGULAR) return fail(c, DDM_E_SINGULAR, "zero or non-finite pivot in a subdomain factor");
+  return DDM_OK;
+}
+
+// =====================================================================================
+// set-up
+// =====================================================================================
+extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double* c_dev, void* stream, ddm_ctx** out) {
+  ddm_ctx* c = nullptr;
+  if (!p || !out || !c_dev) return fail(nullptr, DDM_E_INVAL, "null argument");
+  *out = nullptr;
+  if (p->dim != 2 && p->dim != 3) return fail(nullptr, DDM_E_INVAL, "dim must be 2 or 3");
+  if (p->dim != 2) return fail(nullptr, DDM_E_INVAL, "this build factors 2D subdomains only");
+  if (p->overlap < 1 || p->pml < 1) return fail(nullptr, DDM_E_INVAL, "overlap and pml must be >= 1");
+  if (!(p->h > 0) || !(omega > 0) || p->sigma0 < 0) return fail(nullptr, DDM_E_INVAL, "h, omega must be > 0, sigma0 >= 0");
+  if (p->precision != DDM_FP64 && p->precision != DDM_MIXED) return fail(nullptr, DDM_E_INVAL, "bad precision");
+  if (p->max_rhs < 1 || p->max_rhs > 4096) return fail(nullptr, DDM_E_INVAL, "max_rhs must be in [1, 4096]");
+  c = new ddm_ctx();
+  c->p = *p;
+  c->omega = omega;
+  c->st = (cudaStream_t)stream;
+  c->dim = p->dim;
+  c->e = p->overlap + p->pml;
+  c->prec = p->precision;
+  const int d = c->dim, e = c->e, ov = p->overlap;
+  Geom& g = c->g;
+  memset(&g, 0, sizeof(g));
+  g.dim = d; g.e = e; g.ov = ov; g.h2 = p->h * p->h;
+  // cuts
+  for (int a = 0; a < 3; ++a) {
+    if (a >= d) { g.N[a] = 1; g.parts[a] = 1; continue; }
+    if (p->n[a] < 1 || p->parts[a] < 1 || p->parts[a] > 4096) { delete c; return fail(nullptr, DDM_E_INVAL, "bad n / parts"); }
+    g.N[a] = (int)(p->n[a] + 2 * e);
+    g.parts[a] = p->parts[a];
+    for (int i = 0; i <= p->parts[a]; ++i) {
+      int64_t v = p->cuts[a] ? p->cuts[a][i] : (p->n[a] * i) / p->parts[a];
+      c->cuts_h[a][i] = v;
+    }
+    if (c->cuts_h[a][0] != 0 || c->cuts_h[a][p->parts[a]] != p->n[a]) { delete c; return fail(nullptr, DDM_E_INVAL, "cuts must run from 0 to n"); }
+    for (int i = 0; i < p->parts[a]; ++i) {
+      int64_t w = c->cuts_h[a][i + 1] - c->cuts_h[a][i];
+      if (w < 2 * ov || w < 2) { delete c; return fail(nullptr, DDM_E_INVAL, "every part must be at least 2*overlap nodes wide"); }
+      if (a == 0 && w + 2 * e > 128) { delete c; return fail(nullptr, DDM_E_INVAL, "x-extent of a subdomain (own + 2(overlap+pml)) must be <= 128"); }
+    }
+  }
+  g.nglob = (long long)g.N[0] * g.N[1] * g.N[2];
+  // alpha tables: one per (axis, part), then the global box per axis
+  std::vector<int> tdesc;
+  int tab_total = 0;
+  std::vector<std::vector<int>> part_tab(3);
+  for (int a = 0; a < d; ++a) {
+    for (int i = 0; i < g.parts[a]; ++i) {
+      int lo = (int)c->cuts_h[a][i], hi = (int)c->cuts_h[a][i + 1];
+      part_tab[a].push_back(tab_total);
+      tdesc.push_back(lo); tdesc.push_back(hi); tdesc.push_back(tab_total);
+      tab_total += 2 * (hi - lo + 2 * e) + 1;
+    }
+  }
+  for (int a = 0; a < d; ++a) {
+    g.gtab[a] = tab_total;
+    tdesc.push_back(0); tdesc.push_back((int)p->n[a]); tdesc.push_back(tab_total);
+    tab_total += 2 * (int)(p->n[a] + 2 * e) + 1;
+  }
+  // subdomains, C order (z slowest, x fastest)
+  g.nsub = g.parts[0] * g.parts[1] * g.parts[2];
+  c->subs.resize(g.nsub);
+  long long vofs = 0;
+  for (int sid = 0; sid < g.nsub; ++sid) {
+    SubDesc& s = c->subs[sid];
+    memset(&s, 0, sizeof(s));
+    int idx[3] = {sid % g.parts[0], (sid / g.parts[0]) % g.parts[1], sid / (g.parts[0] * g.parts[1])};
+    for (int a = 0; a < 3; ++a) {
+      s.idx[a] = idx[a];
+      if (a < d) {
+        s.lo[a] = (int)c->cuts_h[a][idx[a]];
+        s.nown[a] = (int)(c->cuts_h[a][idx[a] + 1] - c->cuts_h[a][idx[a]]);
+        s.ext[a] = s.nown[a] + 2 * e;
+        s.tab[a] = part_tab[a][idx[a]];
+        if (idx[a] == 0) s.at_lo |= 1 << a;
+        if (idx[a] == g.parts[a] - 1) s.at_hi |= 1 << a;
+      } else {
+        s.lo[a] = 0; s.nown[a] = 1; s.ext[a] = 1; s.tab[a] = 0;
+      }
+    }
+    s.vofs = vofs;
+    vofs += (long long)s.ext[0] * s.ext[1] * s.ext[2];
+    for (int code = 0; code < NDIR; ++code) {
+      int dd[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+      int nb[3];
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        if (a >= d && dd[a] != 0) ok = false;
+        nb[a] = idx[a] - dd[a];   // the sender sits at R - d (d = direction of propagation)
+        if (nb[a] < 0 || nb[a] >= g.parts[a]) ok = false;
+      }
+      s.nbr[code] = ok ? (nb[2] * g.parts[1] + nb[1]) * g.parts[0] + nb[0] : -1;
+    }
+  }
+  g.ltotal = vofs;
+  // owner tables (global extended index -> part along the axis)
+  std::vector<int> owner;
+  int own_ofs[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a) {
+    own_ofs[a] = (int)owner.size();
+    for (int gi = 0; gi < g.N[a]; ++gi) {
+      if (a >= d) { owner.push_back(0); continue; }
+      int pnode = gi - e, part = 0;
+      while (part + 1 < g.parts[a] && pnode >= c->cuts_h[a][part + 1]) ++part;
+      owner.push_back(part);
+    }
+  }
+  std::vector<int> cutsv;
+  int cut_ofs[3];
+  for (int a = 0; a < 3; ++a) {
+    cut_ofs[a] = (int)cutsv.size();
+    for (int i = 0; i <= g.parts[a]; ++i) cutsv.push_back(a < d ? (int)c->cuts_h[a][i] : i);
+  }
+  // device allocations
+  const int R = p->max_rhs;
+  const size_t le = local_elem(c);
+  int maxlen = 0;
+  for (auto& s : c->subs) maxlen = std::max(maxlen, s.ext[0] * s.ext[1] * s.ext[2]);
+  c->npart = std::max<long long>((long long)R * g.nsub * ((maxlen + 255) / 256), 304LL * 2 * 130);
+  int* d_tdesc = nullptr;
+#define ALLOC(ptr, bytes) CK(cudaMalloc((void**)&(ptr), (bytes)))
+  ddm_status st = DDM_OK;
+  auto body = [&]() -> ddm_status {
+    ALLOC(c->d_k2, sizeof(double) * g.nglob);
+    ALLOC(c->d_tab, sizeof(z64) * tab_total);
+    ALLOC(c->d_beta, sizeof(double) * (ov + 1));
+    ALLOC(c->d_owner, sizeof(int) * owner.size());
+    ALLOC(c->d_cuts, sizeof(int) * cutsv.size());
+    ALLOC(c->d_subs, sizeof(SubDesc) * g.nsub);
+    ALLOC(c->d_err, sizeof(int));
+    ALLOC(c->d_part, sizeof(double) * c->npart);
+    ALLOC(c->d_scal, sizeof(double) * 64);
+    CK(cudaMallocHost((void**)&c->h_scal, sizeof(double) * 64));
+    ALLOC(d_tdesc, sizeof(int) * tdesc.size());
+    ALLOC(c->d_src, le * g.ltotal * R);
+    ALLOC(c->d_U, le * g.ltotal * R);
+    for (int k = 0; k < ring_slots(c); ++k) ALLOC(c->d_ring[k], le * g.ltotal * R);
+    ALLOC(c->d_gb, sizeof(z64) * g.nglob * R);
+    ALLOC(c->d_gr, sizeof(z64) * g.nglob * R);
+    ALLOC(c->d_gw, sizeof(z64) * g.nglob * R);
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+    CK(cudaMemcpyAsync(d_tdesc, tdesc.data(), sizeof(int) * tdesc.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_owner, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_cuts, cutsv.data(), sizeof(int) * cutsv.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDesc) * g.nsub, cudaMemcpyHostToDevice, c->st));
+    g.k2 = c->d_k2; g.tab = c->d_tab; g.beta = c->d_beta; g.subs = c->d_subs;
+    for (int a = 0; a < 3; ++a) { g.owner[a] = c->d_owner + own_ofs[a]; g.cuts[a] = c->d_cuts + cut_ofs[a]; }
+    CK(launch_build_tables(c, d_tdesc, (int)(tdesc.size() / 3), p->sigma0, p->pml_power, p->pml));
+    CK(launch_k2(c, c_dev));
+    CK(launch_beta(c));
+    CK(cudaStreamSynchronize(c->st));
+    return DDM_OK;
+  };
+  st = body();
+  if (d_tdesc) cudaFree(d_tdesc);
+  if (st != DDM_OK) {
+    std::string msg = c->err;
+    ddm_destroy(c);
+    return fail(nullptr, st, msg);
+  }
+  *out = c;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
+  if (!c) return DDM_OK;
+  if (c->st || true) cudaStreamSynchronize(c->st);
+  void* ptrs[] = {c->d_subs, c->d_k2, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
+                  c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
+                  c->d_gr, c->d_gw, c->d_hostbuf, c->d_V, c->d_Z, c->d_H, c->d_gs};
+  for (void* q : ptrs) if (q) cudaFree(q);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
+  for (auto ev : c->ev_pool) cudaEventDestroy(ev);
+  delete c;
+  return DDM_OK;
+}
+
+extern "C" const char* ddm_last_error(const ddm_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
+
+// =====================================================================================
+// factorisation
+// =====================================================================================
+extern "C" ddm_status ddm_factor(ddm_ctx* c) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  Geom& g = c->g;
+  unsigned long long* d_hash = nullptr;
+  CK(cudaMalloc((void**)&d_hash, sizeof(unsigned long long) * g.nsub));
+  CK(launch_sub_hash(c, d_hash));
+  std::vector<unsigned long long> hash(g.nsub);
+  CK(cudaMemcpyAsync(hash.data(), d_hash, sizeof(unsigned long long) * g.nsub, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  cudaFree(d_hash);
+  // group by (own widths, hash); confirm every member against its group's representative
+  std::map<std::tuple<int, int, int, unsigned long long>, int> groups;
+  std::vector<int> rep_of(g.nsub);
+  for (int s = 0; s < g.nsub; ++s) {
+    auto key = std::make_tuple(c->subs[s].nown[0], c->subs[s].nown[1], c->subs[s].nown[2], hash[s]);
+    auto it = groups.find(key);
+    if (it == groups.end()) { groups[key] = s; rep_of[s] = s; }
+    else rep_of[s] = it->second;
+  }
+  std::vector<int> pairs;
+  for (int s = 0; s < g.nsub; ++s) if (rep_of[s] != s) { pairs.push_back(s); pairs.push_back(rep_of[s]); }
+  int npairs = (int)pairs.size() / 2;
+  if (npairs) {
+    int *d_pairs = nullptr, *d_mis = nullptr;
+    CK(cudaMalloc((void**)&d_pairs, sizeof(int) * pairs.size()));
+    CK(cudaMalloc((void**)&d_mis, sizeof(int) * npairs));
+    CK(cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, c->st));
+    CK(launch_sub_compare(c, d_pairs, npairs, d_mis));
+    std::vector<int> mis(npairs);
+    CK(cudaMemcpyAsync(mis.data(), d_mis, sizeof(int) * npairs, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(d_pairs); cudaFree(d_mis);
+    for (int q = 0; q < npairs; ++q) if (mis[q]) rep_of[pairs[2 * q]] = pairs[2 * q];   // hash collision: own factor
+  }
+  // factor ids and storage
+  std::vector<int> fid_of_rep(g.nsub, -1), reps;
+  c->fac_b.clear(); c->fac_m.clear(); c->fac_ldb.clear(); c->fac_ofs.clear();
+  long long ofs = 0;
+  for (int s = 0; s < g.nsub; ++s) {
+    int r = rep_of[s];
+    if (fid_of_rep[r] < 0) {
+      fid_of_rep[r] = (int)reps.size();
+      reps.push_back(r);
+      int b = c->subs[r].ext[0], m = c->subs[r].ext[1];
+      int ldb = (b + 3) & ~3;
+      c->fac_b.push_back(b); c->fac_m.push_back(m); c->fac_ldb.push_back(ldb); c->fac_ofs.push_back(ofs);
+      ofs += (long long)m * b * ldb;
+    }
+    int f = fid_of_rep[r];
+    c->subs[s].fid = f;
+    c->subs[s].fofs = c->fac_ofs[f];
+    c->subs[s].pad = c->fac_ldb[f];
+  }
+  c->nfac = (int)reps.size();
+  c->fac_elems = ofs;
+  if (c->d_G) { cudaFree(c->d_G); c->d_G = nullptr; }
+  CK(cudaMalloc(&c->d_G, ofs * local_elem(c)));
+  CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDesc) * g.nsub, cudaMemcpyHostToDevice, c->st));
+  int *d_reps = nullptr, *d_ldb = nullptr;
+  long long* d_fofs = nullptr;
+  CK(cudaMalloc((void**)&d_reps, sizeof(int) * c->nfac));
+  CK(cudaMalloc((void**)&d_ldb, sizeof(int) * c->nfac));
+  CK(cudaMalloc((void**)&d_fofs, sizeof(long long) * c->nfac));
+  CK(cudaMemcpyAsync(d_reps, reps.data(), sizeof(int) * c->nfac, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(d_ldb, c->fac_ldb.data(), sizeof(int) * c->nfac, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(d_fofs, c->fac_ofs.data(), sizeof(long long) * c->nfac, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->st);
+  {
+    TScope ts(c, T_FACTOR);
+    CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
+  }
+  cudaEventRecord(e1, c->st);
+  CK(cudaStreamSynchronize(c->st));
+  cudaEventElapsedTime(&c->factor_ms, e0, e1);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  cudaFree(d_reps); cudaFree(d_ldb); cudaFree(d_fofs);
+  CKS(check_err_word(c));
+  c->factored = true;
+  return DDM_OK;
+}
+
+// =====================================================================================
+// DDM steps (Algorithm 3.1) and the preconditioner
+// =====================================================================================
+// Runs K steps from the global J-scaled right-hand side b (nrhs vectors).  w_out (global,
+// may be null) receives sum_R beta_0 U_R; res_host[s-1] (may be null, nrhs = 1) the norm of
+// the own-region residual after step s; u_last (may be null) the last step's local solution.
+static ddm_status run_steps(ddm_ctx* c, const z64* b, int nrhs, int K, z64* w_out, double* res_host, void* u_last,
+                            double stop_abs = -1.0, int* steps_done = nullptr) {
+  const int L = ring_slots(c);
+  {
+    TScope ts(c, T_ASSEMBLE);
+    CK(launch_restrict(c, b, c->d_src, c->d_U, nrhs));
+  }
+  int s = 1;
+  for (; s <= K; ++s) {
+    {
+      TScope ts(c, T_SOLVE);
+      CK(launch_local_solve(c, c->d_src, c->d_ring[s % L], c->d_U, nrhs));
+    }
+    const bool want_res = res_host != nullptr;
+    if (s < K || want_res) {
+      int nblk = 0;
+      {
+        TScope ts(c, T_TRANSFER);
+        CK(launch_transfer_n(c, s, c->d_src, c->d_part, nrhs, want_res ? 1 : 0, &nblk));
+      }
+      if (want_res) {
+        // one value: total over all blocks of all receivers
+        CK(launch_sum_partials(c, c->d_part, nblk * c->g.nsub, 1, c->d_scal));
+        CK(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        res_host[s - 1] = std::sqrt(c->h_scal[0]);
+        if (stop_abs >= 0 && res_host[s - 1] <= stop_abs) { ++s; break; }
+      }
+    }
+  }
+  if (steps_done) *steps_done = s - 1;
+  if (u_last) {
+    const int last = s - 1;
+    CK(cudaMemcpyAsync(u_last, c->d_ring[last % L], local_elem(c) * c->g.ltotal * nrhs, cudaMemcpyDeviceToDevice, c->st));
+  }
+  if (w_out) {
+    TScope ts(c, T_ASSEMBLE);
+    CK(launch_assemble(c, c->d_U, w_out, nrhs));
+  }
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_apply(ddm_ctx* c, int K, const void* src_dev, void* dst_dev, int nrhs) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (K < 1 || nrhs < 1 || nrhs > c->p.max_rhs || !src_dev || !dst_dev) return fail(c, DDM_E_INVAL, "bad K / nrhs / pointer");
+  if (!c->factored) return fail(c, DDM_E_STATE, "ddm_factor must run before ddm_apply");
+  CKS(run_steps(c, (const z64*)src_dev, nrhs, K, (z64*)dst_dev, nullptr, nullptr));
+  CK(cudaGetLastError());
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_steps(ddm_ctx* c, const void* b_dev, int nsteps, void* w_dev, void* u_last_dev, double* res_host) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nsteps < 1 || !b_dev) return fail(c, DDM_E_INVAL, "bad nsteps / pointer");
+  if (!c->factored) return fail(c, DDM_E_STATE, "ddm_factor must run first");
+  CKS(run_steps(c, (const z64*)b_dev, 1, nsteps, (z64*)w_dev, res_host, u_last_dev));
+  CK(cudaStreamSynchronize(c->st));
+  return check_err_word(c);
+}
+
+extern "C" ddm_status ddm_local_solve(ddm_ctx* c, const void* src_dev, void* u_dev, int nrhs) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nrhs < 1 || nrhs > c->p.max_rhs) return fail(c, DDM_E_INVAL, "bad nrhs");
+  if (!c->factored) return fail(c, DDM_E_STATE, "ddm_factor must run first");
+  {
+    TScope ts(c, T_SOLVE);
+    CK(launch_local_solve(c, src_dev, u_dev, nullptr, nrhs));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  return check_err_word(c);
+}
+
+// =====================================================================================
+// global operator, residual, right-hand side
+// =====================================================================================
+extern "C" ddm_status ddm_rhs(ddm_ctx* c, const void* f_dev, void* b_dev, int nrhs) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nrhs < 1) return fail(c, DDM_E_INVAL, "bad nrhs");
+  CK(launch_rhs(c, (const z64*)f_dev, (z64*)b_dev, nrhs));
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_global_apply(ddm_ctx* c, const void* x_dev, void* y_dev, int nrhs) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nrhs < 1) return fail(c, DDM_E_INVAL, "bad nrhs");
+  TScope ts(c, T_GLOBAL);
+  CK(launch_global_apply(c, (const z64*)x_dev, (z64*)y_dev, nullptr, nrhs));
+  return DDM_OK;
+}
+
+// norms2_dev[i] = ||x_i||^2 for nvec vectors of length nglob (device doubles)
+static ddm_status norms2(ddm_ctx* c, const z64* x, int nvec, double* norms2_dev) {
+  int nblk = 0;
+  CK(launch_norm2_partial(c, x, c->g.nglob, nvec, c->d_part, &nblk));
+  CK(launch_sum_partials(c, c->d_part, nblk, nvec, norms2_dev));
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_residual(ddm_ctx* c, const void* b_dev, const void* x_dev, void* r_dev, int nrhs, double* norms_host) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nrhs < 1 || nrhs > 16) return fail(c, DDM_E_INVAL, "nrhs must be in [1, 16]");
+  {
+    TScope ts(c, T_GLOBAL);
+    CK(launch_global_apply(c, (const z64*)x_dev, (z64*)r_dev, (const z64*)b_dev, nrhs));
+  }
+  if (norms_host) {
+    CKS(norms2(c, (const z64*)r_dev, nrhs, c->d_scal));
+    CKS(norms2(c, (const z64*)b_dev, nrhs, c->d_scal + 16));
+    CK(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double) * 32, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < nrhs; ++i) {
+      norms_host[2 * i] = std::sqrt(c->h_scal[i]);
+      norms_host[2 * i + 1] = std::sqrt(c->h_scal[16 + i]);
+    }
+  }
+  return DDM_OK;
+}
+
+// =====================================================================================
+// solvers
+// =====================================================================================
+static double host_norm(ddm_ctx* c, const z64* x, ddm_status* st) {
+  *st = norms2(c, x, 1, c->d_scal + 32);
+  if (*st != DDM_OK) return 0;
+  cudaMemcpyAsync(c->h_scal + 32, c->d_scal + 32, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) { *st = fail(c, DDM_E_CUDA, cudaGetErrorString(e)); return 0; }
+  return std::sqrt(c->h_scal[32]);
+}
+
+static ddm_status ensure_krylov(ddm_ctx* c, int m) {
+  if (c->kry_m >= m) return DDM_OK;
+  if (c->d_V) { cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_H); cudaFree(c->d_gs); }
+  c->d_V = c->d_Z = c->d_H = c->d_gs = nullptr;
+  c->kry_m = 0;
+  CK(cudaMalloc((void**)&c->d_V, sizeof(z64) * c->g.nglob * (m + 1)));
+  CK(cudaMalloc((void**)&c->d_Z, sizeof(z64) * c->g.nglob * m));
+  CK(cudaMalloc((void**)&c->d_H, sizeof(z64) * (m + 1) * m));
+  CK(cudaMalloc((void**)&c->d_gs, sizeof(z64) * (5 * m + 4)));
+  c->kry_m = m;
+  return DDM_OK;
+}
+
+// Flexible GMRES(m) for A x = b (one right-hand side), right-preconditioned by M_K.
+static ddm_status fgmres_one(ddm_ctx* c, const z64* b, z64* x, double tol, int max_it, int K, int m, ddm_info* info) {
+  const long long n = c->g.nglob;
+  ddm_status st;
+  CKS(ensure_krylov(c, m));
+  double bnorm = host_norm(c, b, &st);
+  if (st != DDM_OK) return st;
+  CK(cudaMemsetAsync(x, 0, sizeof(z64) * n, c->st));
+  if (bnorm == 0.0) { if (info) { info->converged = 1; info->rel_residual = 0; } return DDM_OK; }
+  z64* V = c->d_V;
+  z64* Z = c->d_Z;
+  z64* H = c->d_H;
+  z64* gs = c->d_gs;
+  z64* coef = gs + 4 * m + 2;
+  int it = 0, steps = 0;
+  double est = 1.0;
+  bool conv = false;
+  while (it < max_it && !conv) {
+    {
+      TScope ts(c, T_GLOBAL);
+      CK(launch_global_apply(c, x, c->d_gr, b, 1));
+    }
+    double beta = host_norm(c, c->d_gr, &st);
+    if (st != DDM_OK) return st;
+    est = beta / bnorm;
+    if (est <= tol) { conv = true; break; }
+    CK(launch_copy_scaled(c, c->d_gr, 1.0 / beta, V, n));
+    CK(cudaMemsetAsync(gs, 0, sizeof(z64) * (5 * m + 4), c->st));
+    CK(cudaMemsetAsync(H, 0, sizeof(z64) * (m + 1) * m, c->st));
+    z64 g0 = mk<double>(beta, 0.0);
+    CK(cudaMemcpyAsync(gs + 2 * m, &g0, sizeof(z64), cudaMemcpyHostToDevice, c->st));
+    int j = 0;
+    for (; j < m && it < max_it; ++j) {
+      z64* vj = V + (long long)j * n;
+      z64* zj = Z + (long long)j * n;
+      z64* w = V + (long long)(j + 1) * n;
+      CKS(run_steps(c, vj, 1, K, zj, nullptr, nullptr));
+      steps += K;
+      {
+        TScope ts(c, T_GLOBAL);
+        CK(launch_global_apply(c, zj, w, nullptr, 1));
+      }
+      {
+        TScope ts(c, T_KRYLOV);
+        for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+          int nblk = 0;
+          CK(launch_dots(c, V, j + 1, w, n, c->d_part, &nblk));
+          CK(launch_arnoldi_coef(c, c->d_part, nblk, j + 1, H + (long long)j * (m + 1), coef, pass == 0));
+          CK(launch_sub_axpy(c, V, j + 1, coef, w, n));
+        }
+        int nblk = 0;
+        CK(launch_norm2_partial(c, w, n, 1, c->d_part, &nblk));
+        CK(launch_sum_partials(c, c->d_part, nblk, 1, c->d_scal + 40));
+        CK(launch_givens(c, j, m, c->d_scal + 40, H, gs, c->d_scal + 41));
+        CK(launch_scale(c, w, gs + 3 * m + 1, w, n));
+      }
+      CK(cudaMemcpyAsync(c->h_scal + 41, c->d_scal + 41, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      ++it;
+      est = c->h_scal[41] / bnorm;
+      if (!(est == est)) return fail(c, DDM_E_NOCONV, "non-finite residual estimate in FGMRES");
+      if (est <= tol) { ++j; conv = true; break; }
+    }
+    {
+      TScope ts(c, T_KRYLOV);
+      CK(launch_lsq_update(c, j, m, H, gs, Z, x, n));
+    }
+  }
+  if (info) { info->iters += it; info->ddm_steps += steps; info->rel_residual_est = est; }
+  return DDM_OK;
+}
+
+// Algorithm 3.1 continued as an iteration (Section 4.2.1).  FP64: steps until the own-region
+// residual (from the transfers) <= tol ||b||.  Mixed: iterative refinement x += M(r) with the
+// inner complex64 iteration run to a relative 1e-4 (or stagnation), r = b - A x in FP64.
+static ddm_status stepping_one(ddm_ctx* c, const z64* b, z64* x, double tol, int max_steps, ddm_info* info) {
+  const long long n = c->g.nglob;
+  ddm_status st;
+  double bnorm = host_norm(c, b, &st);
+  if (st != DDM_OK) return st;
+  CK(cudaMemsetAsync(x, 0, sizeof(z64) * n, c->st));
+  if (bnorm == 0.0) return DDM_OK;
+  std::vector<double> hist(max_steps + 1);
+  int total = 0;
+  const bool mixed = c->prec == DDM_MIXED;
+  const z64* rhs = b;
+  double rnorm = bnorm;
+  double est = 1.0;
+  for (int outer = 0; outer < 64 && total < max_steps; ++outer) {
+    double inner_tol = mixed ? std::max(tol * bnorm / rnorm * 0.5, 1e-4) : tol * bnorm / rnorm;
+    int done = 0;
+    CKS(run_steps(c, rhs, 1, max_steps - total, c->d_gw, hist.data(), nullptr, inner_tol * rnorm, &done));
+    total += done;
+    est = hist[std::max(done - 1, 0)] / bnorm;
+    if (!mixed) {
+      CK(cudaMemcpyAsync(x, c->d_gw, sizeof(z64) * n, cudaMemcpyDeviceToDevice, c->st));
+      break;
+    }
+    // x += w; r = b - A x (FP64)
+    {
+      TScope ts(c, T_KRYLOV);
+      CK(launch_axpy(c, 1.0, c->d_gw, x, n));
+    }
+    {
+      TScope ts(c, T_GLOBAL);
+      CK(launch_global_apply(c, x, c->d_gr, b, 1));
+    }
+    rnorm = host_norm(c, c->d_gr, &st);
+    if (st != DDM_OK) return st;
+    est = rnorm / bnorm;
+    if (est <= tol) break;
+    rhs = c->d_gr;
+  }
+  if (info) { info->iters += total; info->ddm_steps += total; info->rel_residual_est = est; }
+  return DDM_OK;
+}
+
+static ddm_status solve_impl(ddm_ctx* c, const void* f_dev, void* u_dev, int nrhs, double tol, int max_it, int mode,
+                             int K, int restart, ddm_info* info) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nrhs < 1 || nrhs > c->p.max_rhs || !f_dev || !u_dev) return fail(c, DDM_E_INVAL, "bad nrhs / pointer");
+  if (!(tol > 0) || max_it < 1) return fail(c, DDM_E_INVAL, "tol must be > 0 and max_it >= 1");
+  if (mode != DDM_FGMRES && mode != DDM_STEPPING) return fail(c, DDM_E_INVAL, "bad mode");
+  if (mode == DDM_FGMRES && (K < 1 || restart < 1 || restart > 120)) return fail(c, DDM_E_INVAL, "K >= 1 and restart in [1, 120]");
+  if (!c->factored) return fail(c, DDM_E_STATE, "ddm_factor must run before ddm_solve");
+  auto t0 = std::chrono::steady_clock::now();
+  ddm_info loc;
+  memset(&loc, 0, sizeof(loc));
+  const long long n = c->g.nglob;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+  CK(launch_rhs(c, (const z64*)f_dev, c->d_gb, nrhs));
+  double worst = 0.0;
+  bool all_conv = true;
+  for (int r = 0; r < nrhs; ++r) {
+    const z64* b = c->d_gb + (long long)r * n;
+    z64* x = (z64*)u_dev + (long long)r * n;
+    if (mode == DDM_FGMRES) CKS(fgmres_one(c, b, x, tol, max_it, K, restart, &loc));
+    else CKS(stepping_one(c, b, x, tol, max_it, &loc));
+    double nr[2];
+    CKS(ddm_residual(c, b, x, c->d_gr, 1, nr));
+    double rel = nr[1] > 0 ? nr[0] / nr[1] : 0.0;
+    worst = std::max(worst, rel);
+    if (!(rel <= tol * 1.0001)) all_conv = false;
+  }
+  CK(cudaStreamSynchronize(c->st));
+  auto t1 = std::chrono::steady_clock::now();
+  loc.rel_residual = worst;
+  loc.converged = all_conv ? 1 : 0;
+  loc.n_unique_factors = c->nfac;
+  loc.factor_ms = c->factor_ms;
+  loc.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  if (info) *info = loc;
+  CKS(check_err_word(c));
+  if (!all_conv) return fail(c, DDM_E_NOCONV, "tolerance not reached (explicit residual " + std::to_string(worst) + ")");
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_solve(ddm_ctx* c, const void* f_dev, void* u_dev, int nrhs, double tol, int max_it, int mode,
+                                int K, int restart, ddm_info* info) {
+  return solve_impl(c, f_dev, u_dev, nrhs, tol, max_it, mode, K, restart, info);
+}
+
+extern "C" ddm_status ddm_solve_host(ddm_ctx* c, const void* f_host, void* u_host, int nrhs, double tol, int max_it,
+                                     int mode, int K, int restart, ddm_info* info) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nrhs < 1 || nrhs > c->p.max_rhs || !f_host || !u_host) return fail(c, DDM_E_INVAL, "bad nrhs / pointer");
+  const long long n = c->g.nglob;
+  if (!c->d_hostbuf) CK(cudaMalloc((void**)&c->d_hostbuf, sizeof(z64) * n * c->p.max_rhs * 2));
+  z64* f = c->d_hostbuf;
+  z64* u = c->d_hostbuf + n * c->p.max_rhs;
+  CK(cudaMemcpyAsync(f, f_host, sizeof(z64) * n * nrhs, cudaMemcpyHostToDevice, c->st));
+  ddm_status st = solve_impl(c, f, u, nrhs, tol, max_it, mode, K, restart, info);
+  CK(cudaMemcpyAsync(u_host, u, sizeof(z64) * n * nrhs, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return st;
+}
+
+// =====================================================================================
+// introspection
+// =====================================================================================
+extern "C" ddm_status ddm_local_layout(const ddm_ctx* c, int* n_sub, int64_t* total, int64_t* offsets, int* ext_x,
+                                       int* ext_y, int* ext_z) {
+  if (!c) return DDM_E_INVAL;
+  if (n_sub) *n_sub = c->g.nsub;
+  if (total) *total = c->g.ltotal;
+  for (int s = 0; s < c->g.nsub; ++s) {
+    if (offsets) offsets[s] = c->subs[s].vofs;
+    if (ext_x) ext_x[s] = c->subs[s].ext[0];
+    if (ext_y) ext_y[s] = c->subs[s].ext[1];
+    if (ext_z) ext_z[s] = c->subs[s].ext[2];
+  }
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_timing(ddm_ctx* c, int enable, int reset, double* out_ms, int64_t* out_launches) {
+  if (!c) return DDM_E_INVAL;
+  timing_drain(c);
+  if (out_ms) for (int i = 0; i < T_NSLOT; ++i) out_ms[i] = c->t_ms[i];
+  if (out_launches) for (int i = 0; i < T_NSLOT; ++i) out_launches[i] = c->t_n[i];
+  if (reset) for (int i = 0; i < T_NSLOT; ++i) { c->t_ms[i] = 0; c->t_n[i] = 0; }
+  c->timing = enable != 0;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_factor_bytes(const ddm_ctx* c, int64_t* per_solve, int64_t* stored) {
+  if (!c || !c->factored) return DDM_E_STATE;
+  const long long el = (long long)local_elem(c);
+  long long ps = 0;
+  for (auto& s : c->subs) {
+    long long b = s.ext[0], m = s.ext[1];
+    ps += (2 * m - 1) * b * b * el;
+  }
+  if (per_solve) *per_solve = ps;
+  if (stored) *stored = c->fac_elems * el;
+  return DDM_OK;
+}

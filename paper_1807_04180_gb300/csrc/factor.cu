@@ -1,0 +1,170 @@
+// Factorisation of the subdomain PML operators (the local problems of Algorithm 3.1).
+//
+// A subdomain operator in natural ordering (x fastest) is block tridiagonal over its
+// x-lines: diagonal blocks T_k (tridiagonal, x-couplings of line k) and diagonal
+// off-diagonal blocks L_k = diag(c_S(., k)), U_k = diag(c_N(., k)).  Block elimination
+// gives D_0 = T_0, D_k = T_k - L_k D_{k-1}^{-1} U_{k-1}; the factor stores
+// G_k = D_k^{-1} (dense b x b, row-major, leading dimension ldb), inverted in shared memory
+// by Gauss-Jordan elimination with partial (row) pivoting inside the block.  One CTA per
+// distinct factor walks the lines sequentially.
+#include <algorithm>
+
+#include "ddm_internal.cuh"
+
+namespace ddm {
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const long long* fofs_arr,
+                                                  const int* ldbs, cplx<T>* Gout, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SubDesc& s = g.subs[reps[blockIdx.x]];
+  const long long fofs = fofs_arr[blockIdx.x];
+  const int ldb = ldbs[blockIdx.x];
+  const int b = s.ext[0], m = s.ext[1];
+  cplx<T>* M = (cplx<T>*)smem;               // b x ldb working block
+  cplx<T>* colp = M + (long long)b * ldb;    // column p multipliers
+  cplx<T>* cC = colp + b;                    // centre of line k
+  cplx<T>* cE = cC + b;                      // x+ coupling
+  cplx<T>* cW = cE + b;                      // x- coupling
+  cplx<T>* cS = cW + b;                      // coupling of line k to line k-1
+  cplx<T>* cNp = cS + b;                     // coupling of line k-1 to line k
+  cplx<T>* cNn = cNp + b;
+  int* perm = (int*)(cNn + b);
+  int* cm = perm + b;
+  __shared__ int s_piv, s_bad;
+  __shared__ cplx<T> s_inv;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  if (tid == 0) s_bad = 0;
+  for (int j = tid; j < b; j += nth) cm[j] = j;
+  __syncthreads();
+
+  for (int k = 0; k < m; ++k) {
+    // coefficients of line k (FP64 evaluation, cast to T)
+    for (int i = tid; i < b; i += nth) {
+      int x[3] = {i, k, 0};
+      long long gi = (long long)(s.lo[1] + k) * g.N[0] + (s.lo[0] + i);
+      Coef cf = coef_at(g, s.tab, s.ext, x, g.k2[gi]);
+      cC[i] = ccast<T>(cf.c); cE[i] = ccast<T>(cf.p[0]); cW[i] = ccast<T>(cf.m[0]);
+      cS[i] = ccast<T>(cf.m[1]); cNn[i] = ccast<T>(cf.p[1]);
+    }
+    __syncthreads();
+    // D_k = T_k - L_k G_{k-1} U_{k-1}; rows are rebuilt warp-wise (read the whole row of
+    // G_{k-1} through the column map first, then overwrite), and G_{k-1} is written out.
+    for (int i = warp; i < b; i += nwarp) {
+      cplx<T> v[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        int j = lane + 32 * jj;
+        v[jj] = (k > 0 && j < b) ? M[(long long)i * ldb + cm[j]] : mk<T>(0, 0);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        int j = lane + 32 * jj;
+        if (j < b) {
+          if (k > 0) Gout[fofs + ((long long)(k - 1) * b + i) * ldb + j] = v[jj];
+          cplx<T> d = mk<T>(0, 0);
+          if (k > 0) d = -(cS[i] * v[jj] * cNp[j]);
+          if (j == i) d = d + cC[i];
+          if (j == i + 1) d = d + cE[i];
+          if (j == i - 1) d = d + cW[i];
+          M[(long long)i * ldb + j] = d;
+        } else if (j < ldb && k > 0) {
+          Gout[fofs + ((long long)(k - 1) * b + i) * ldb + j] = mk<T>(0, 0);
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j < b; j += nth) cNp[j] = cNn[j];   // read by the next line's build only
+
+    // Gauss-Jordan inversion with partial pivoting, in place
+    for (int p = 0; p < b; ++p) {
+      if (warp == 0) {
+        T best = (T)-1; int bi = p;
+        for (int i = p + lane; i < b; i += 32) {
+          T a = cabs2(M[(long long)i * ldb + p]);
+          if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o; o >>= 1) {
+          T ob = __shfl_xor_sync(0xffffffffu, best, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          s_piv = bi;
+          cplx<T> pv = M[(long long)bi * ldb + p];
+          if (!(best > (T)0) || !isfinite(best)) { s_bad = 1; s_inv = mk<T>(0, 0); }
+          else s_inv = cinv(pv);
+          perm[p] = bi;
+        }
+      }
+      __syncthreads();
+      const int r = s_piv;
+      const cplx<T> inv = s_inv;
+      // phase A: read row p, row r and column p (after the interchange)
+      cplx<T> ap = mk<T>(0, 0), ar = mk<T>(0, 0), cpv = mk<T>(0, 0);
+      if (tid < b) {
+        ap = M[(long long)p * ldb + tid];
+        ar = M[(long long)r * ldb + tid];
+        int i = tid;
+        cpv = (i == p) ? mk<T>(0, 0) : (i == r ? M[(long long)p * ldb + p] : M[(long long)i * ldb + p]);
+      }
+      __syncthreads();
+      // phase B: interchange, scale the pivot row, keep the multipliers
+      if (tid < b) {
+        int j = tid;
+        cplx<T> nr = (j == p) ? inv : ar * inv;
+        M[(long long)p * ldb + j] = nr;
+        if (r != p) M[(long long)r * ldb + j] = ap;
+        colp[j] = cpv;
+      }
+      __syncthreads();
+      // phase C: eliminate column p from every other row
+      for (int idx = tid; idx < b * b; idx += nth) {
+        int i = idx / b, j = idx - i * b;
+        if (i == p) continue;
+        cplx<T> mp = M[(long long)p * ldb + j];
+        cplx<T> cur = (j == p) ? mk<T>(0, 0) : M[(long long)i * ldb + j];
+        M[(long long)i * ldb + j] = cur - colp[i] * mp;
+      }
+      __syncthreads();
+    }
+    // column map undoing the interchanges (applied when the block is read)
+    if (tid == 0) {
+      for (int j = 0; j < b; ++j) cm[j] = j;
+      for (int p = b - 1; p >= 0; --p) { int q = perm[p]; int t = cm[p]; cm[p] = cm[q]; cm[q] = t; }
+    }
+    __syncthreads();
+  }
+  // write the last block
+  for (int i = warp; i < b; i += nwarp)
+    for (int j = lane; j < ldb; j += 32)
+      Gout[fofs + ((long long)(m - 1) * b + i) * ldb + j] = (j < b) ? M[(long long)i * ldb + cm[j]] : mk<T>(0, 0);
+  if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
+}
+
+size_t factor_smem_bytes(int b, int ldb, int prec) {
+  size_t el = prec == DDM_MIXED ? sizeof(c32) : sizeof(z64);
+  return (size_t)b * ldb * el + 7 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
+}
+
+// All distinct factors in one launch, one CTA each.  d_reps[f] is a subdomain using factor
+// f, d_fofs[f] / d_ldb[f] its storage offset and leading dimension.
+cudaError_t launch_factor_all(ddm_ctx* c, const int* d_reps, const long long* d_fofs, const int* d_ldb) {
+  size_t sm = 0;
+  for (int f = 0; f < c->nfac; ++f) sm = std::max(sm, factor_smem_bytes(c->fac_b[f], c->fac_ldb[f], c->prec));
+  cudaError_t e;
+  if (c->prec == DDM_MIXED) {
+    e = cudaFuncSetAttribute(k_factor2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_factor2d<float><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
+  } else {
+    e = cudaFuncSetAttribute(k_factor2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_factor2d<double><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (z64*)c->d_G, c->d_err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ddm

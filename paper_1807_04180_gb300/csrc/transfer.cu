@@ -1,0 +1,274 @@
+// Source restriction, the fused directional-residual transfer (the Psi operators of
+// Section 2.2 in Eq. (talg_2)) with residual-norm partials, and the assembly of the DDM
+// solution (Eq. (tsum)).
+#include "ddm_internal.cuh"
+
+namespace ddm {
+
+__device__ __forceinline__ void unflat(long long i, const int* ext, int* x) {
+  x[0] = (int)(i % ext[0]);
+  x[1] = (int)((i / ext[0]) % ext[1]);
+  x[2] = (int)(i / ((long long)ext[0] * ext[1]));
+}
+
+__device__ __forceinline__ long long flat(const int* x, const int* ext) {
+  return ((long long)x[2] * ext[1] + x[1]) * ext[0] + x[0];
+}
+
+__device__ __forceinline__ long long gflat(const Geom& g, const SubDesc& s, const int* x) {
+  return ((long long)(s.lo[2] + x[2]) * g.N[1] + (s.lo[1] + x[1])) * g.N[0] + (s.lo[0] + x[0]);
+}
+
+// x in the own region of s: own box, continued through the global band on boundary sides
+__device__ __forceinline__ bool in_own(const Geom& g, const SubDesc& s, const int* x) {
+  for (int a = 0; a < g.dim; ++a) {
+    int lo = g.e, hi = g.e + s.nown[a];
+    if (x[a] < lo && !((s.at_lo >> a) & 1)) return false;
+    if (x[a] >= hi && !((s.at_hi >> a) & 1)) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// step-1 source f_ij = b chi_own (Section 2.2), cast to the local precision; zero U.
+// grid: (ceil(maxlen/256), nsub, nrhs)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_restrict(Geom g, const z64* b, cplx<T>* src, cplx<T>* U) {
+  const SubDesc& s = g.subs[blockIdx.y];
+  long long len = (long long)s.ext[0] * s.ext[1] * s.ext[2];
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  int r = blockIdx.z;
+  int x[3];
+  unflat(i, s.ext, x);
+  cplx<T> v = mk<T>(0, 0);
+  if (in_own(g, s, x)) v = ccast<T>(b[(long long)r * g.nglob + gflat(g, s, x)]);
+  long long o = (long long)r * g.ltotal + s.vofs + i;
+  src[o] = v;
+  if (U) U[o] = mk<T>(0, 0);
+}
+
+template <typename T>
+static cudaError_t restrict_t(ddm_ctx* c, const z64* b, void* src, void* U, int nrhs) {
+  int maxlen = 0;
+  for (auto& s : c->subs) maxlen = max(maxlen, s.ext[0] * s.ext[1] * s.ext[2]);
+  dim3 grid((maxlen + 255) / 256, c->g.nsub, nrhs);
+  k_restrict<T><<<grid, 256, 0, c->st>>>(c->g, b, (cplx<T>*)src, (cplx<T>*)U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(ddm_ctx* c, const z64* b, void* src, void* U, int nrhs) {
+  return c->prec == DDM_MIXED ? restrict_t<float>(c, b, src, U, nrhs) : restrict_t<double>(c, b, src, U, nrhs);
+}
+
+// ---------------------------------------------------------------------------
+// Fused transfer.  For receiver R (blockIdx.y) and its extended node x:
+//   src^{s+1}_R(x) = sum_d Psi_d(u_{R-d}^{s+1-lag(d)})(x)
+//   res(x)         = sum_d Psi_d(u^s + .. + u^{s-lag(d)+1})(x)  on R's own region,
+// with Psi_d(v) = -A_R(beta_d v) chi_d, beta_d the sender's cut-off(s) facing R and chi_d
+// the receiver's side of the shared face(s) (Section 2.2).  Psi_d is non-zero only on
+// receiver nodes at most ov nodes inside each shared face.  Sums of |res|^2 per block go to
+// part[(r * nsub + R) * gridDim.x + blockIdx.x].
+// ring[t % L] holds u^t (local layout), L = dim; res_slot[k] is the slot of u^{s-k}
+// (-1 when s-k < 1, i.e. u = 0).
+// ---------------------------------------------------------------------------
+struct RingPtrs { const void* p[3]; int res_slot[3]; };
+
+template <typename T>
+__device__ __forceinline__ cplx<T> beta_u(const Geom& g, const SubDesc& S, const int* d, const int* y,
+                                          const cplx<T>* u) {
+  // beta_d(y) u_S(y) at S-local node y (zero outside S's grid)
+  double b = 1.0;
+  for (int a = 0; a < g.dim; ++a) {
+    if (y[a] < 0 || y[a] >= S.ext[a]) return mk<T>(0, 0);
+    if (d[a] > 0) {            // sender's high-side cut-off beta_{->}: q = y - (e + nown)
+      int q = y[a] - (g.e + S.nown[a]);
+      b *= (q < 0) ? 1.0 : (q >= g.ov ? 0.0 : g.beta[q]);
+    } else if (d[a] < 0) {     // sender's low-side cut-off beta_{<-}: q = (e - 1) - y
+      int q = (g.e - 1) - y[a];
+      b *= (q < 0) ? 1.0 : (q >= g.ov ? 0.0 : g.beta[q]);
+    }
+  }
+  if (b == 0.0) return mk<T>(0, 0);
+  cplx<T> v = u[flat(y, S.ext)];
+  return mk<T>((T)b * v.x, (T)b * v.y);
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> psi_at(const Geom& g, const SubDesc& R, const SubDesc& S, const int* d,
+                                          const int* x, const Coef& cf, const cplx<T>* uS) {
+  // -(A_R (beta_d u_S))(x): 5/7-point stencil of R at x applied to beta_d u_S
+  int shift[3];
+  for (int a = 0; a < 3; ++a) shift[a] = R.lo[a] - S.lo[a];   // R-local -> S-local
+  int y[3] = {x[0] + shift[0], x[1] + shift[1], x[2] + shift[2]};
+  cplx<T> acc = mk<T>(0, 0);
+  cfma(acc, ccast<T>(cf.c), beta_u<T>(g, S, d, y, uS));
+  for (int a = 0; a < g.dim; ++a) {
+    if (x[a] + 1 < R.ext[a]) { y[a] += 1; cfma(acc, ccast<T>(cf.p[a]), beta_u<T>(g, S, d, y, uS)); y[a] -= 1; }
+    if (x[a] > 0) { y[a] -= 1; cfma(acc, ccast<T>(cf.m[a]), beta_u<T>(g, S, d, y, uS)); y[a] += 1; }
+  }
+  return -acc;
+}
+
+template <typename T>
+__global__ void k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res) {
+  const int Rid = blockIdx.y;
+  const SubDesc& R = g.subs[Rid];
+  const int r = blockIdx.z;
+  long long len = (long long)R.ext[0] * R.ext[1] * R.ext[2];
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double res2 = 0.0;
+  if (i < len) {
+    int x[3];
+    unflat(i, R.ext, x);
+    // depth of x inside each face: q_lo = x - e (for d = +1), q_hi = e + nown - 1 - x (d = -1)
+    bool near = false;
+    for (int a = 0; a < g.dim; ++a) {
+      int ql = x[a] - g.e, qh = g.e + R.nown[a] - 1 - x[a];
+      if ((ql >= 0 && ql <= g.ov && !((R.at_lo >> a) & 1)) || (qh >= 0 && qh <= g.ov && !((R.at_hi >> a) & 1)))
+        near = true;
+    }
+    cplx<T> acc_src = mk<T>(0, 0);
+    cplx<T> acc_res = mk<T>(0, 0);
+    if (near) {
+      int xg[3] = {R.lo[0] + x[0], R.lo[1] + x[1], R.lo[2] + x[2]};
+      double k2v = g.k2[((long long)xg[2] * g.N[1] + xg[1]) * g.N[0] + xg[0]];
+      Coef cf = coef_at(g, R.tab, R.ext, x, k2v);
+      for (int code = 0; code < NDIR; ++code) {
+        if (code == 13) continue;
+        int d[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+        if (g.dim == 2 && d[2] != 0) continue;
+        int Sid = R.nbr[code];
+        if (Sid < 0) continue;
+        bool ok = true;
+        int lagd = 0;
+        for (int a = 0; a < g.dim; ++a) {
+          if (d[a] > 0) { int q = x[a] - g.e; ok = ok && q >= 0 && q <= g.ov; ++lagd; }
+          else if (d[a] < 0) { int q = g.e + R.nown[a] - 1 - x[a]; ok = ok && q >= 0 && q <= g.ov; ++lagd; }
+        }
+        if (!ok) continue;
+        const SubDesc& S = g.subs[Sid];
+        // p_k = Psi_d(u^{s-k}), k = 0..lag-1: the source for step s+1 takes k = lag-1
+        // (u^{s+1-lag}); the residual sums all of them.
+        for (int k = 0; k < lagd; ++k) {
+          if (!want_res && k != lagd - 1) continue;
+          int sl = ring.res_slot[k];
+          if (sl < 0) continue;
+          const cplx<T>* u = (const cplx<T>*)ring.p[sl] + (long long)r * g.ltotal + S.vofs;
+          cplx<T> pv = psi_at<T>(g, R, S, d, x, cf, u);
+          if (k == lagd - 1) acc_src = acc_src + pv;
+          acc_res = acc_res + pv;
+        }
+      }
+      if (want_res && in_own(g, R, x)) res2 = (double)acc_res.x * acc_res.x + (double)acc_res.y * acc_res.y;
+    }
+    src_next[(long long)r * g.ltotal + R.vofs + i] = acc_src;
+  }
+  if (want_res) {
+    for (int o = 16; o; o >>= 1) res2 += __shfl_xor_sync(0xffffffffu, res2, o);
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = res2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      part[((long long)r * g.nsub + Rid) * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+int ring_slots(const ddm_ctx* c) { return c->dim; }
+
+// s = index of the step just solved (u^s in ring[s % L]).
+template <typename T>
+static cudaError_t transfer_t(ddm_ctx* c, int s, void* src_next, double* part, int nrhs, int want_res, int* nblk) {
+  int L = ring_slots(c);
+  RingPtrs rp;
+  for (int k = 0; k < 3; ++k) rp.p[k] = c->d_ring[k];
+  // slots of u^s, u^{s-1}, u^{s-2} (-1 where the step index is < 1)
+  for (int k = 0; k < 3; ++k) {
+    int t = s - k;
+    rp.res_slot[k] = (k < L && t >= 1) ? (t % L) : -1;
+  }
+  int maxlen = 0;
+  for (auto& sd : c->subs) maxlen = max(maxlen, sd.ext[0] * sd.ext[1] * sd.ext[2]);
+  dim3 grid((maxlen + 255) / 256, c->g.nsub, nrhs);
+  if (nblk) *nblk = grid.x;
+  k_transfer<T><<<grid, 256, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_n(ddm_ctx* c, int s, void* src_next, double* part, int nrhs, int want_res, int* nblk) {
+  return c->prec == DDM_MIXED ? transfer_t<float>(c, s, src_next, part, nrhs, want_res, nblk)
+                              : transfer_t<double>(c, s, src_next, part, nrhs, want_res, nblk);
+}
+
+
+// ---------------------------------------------------------------------------
+// w = sum_R beta_{0;R} U_R (Eq. (tsum)) on the global grid.  A global node lies in the
+// support of beta_{0;R} for at most two parts per axis: its owner and the neighbour whose
+// face is within ov nodes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cut_lo(const Geom& g, int part, int a, int p) {
+  // beta_{<-} of part along axis a at global node p
+  if (part == 0) return 1.0;
+  int q = g.cuts[a][part] - 1 - p;
+  return q < 0 ? 1.0 : (q >= g.ov ? 0.0 : g.beta[q]);
+}
+__device__ __forceinline__ double cut_hi(const Geom& g, int part, int a, int p) {
+  if (part == g.parts[a] - 1) return 1.0;
+  int q = p - g.cuts[a][part + 1];
+  return q < 0 ? 1.0 : (q >= g.ov ? 0.0 : g.beta[q]);
+}
+
+template <typename T>
+__global__ void k_assemble(Geom g, const cplx<T>* U, z64* w, int nrhs) {
+  long long n = g.nglob;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nrhs; i += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(i / n);
+    long long gi = i % n;
+    int xg[3] = {(int)(gi % g.N[0]), (int)((gi / g.N[0]) % g.N[1]), (int)(gi / ((long long)g.N[0] * g.N[1]))};
+    int cand[3][2], ncand[3], wts_n = 1;
+    double wt[3][2];
+    for (int a = 0; a < 3; ++a) {
+      ncand[a] = 0;
+      if (a >= g.dim) { cand[a][0] = 0; wt[a][0] = 1.0; ncand[a] = 1; continue; }
+      int p = xg[a] - g.e;                     // global node index
+      int own = g.owner[a][xg[a]];
+      for (int dp = -1; dp <= 1; ++dp) {
+        int part = own + dp;
+        if (part < 0 || part >= g.parts[a]) continue;
+        double bwt = cut_lo(g, part, a, p) * cut_hi(g, part, a, p);
+        // nodes outside the part's extended grid carry no value
+        if (p < g.cuts[a][part] - g.e || p >= g.cuts[a][part + 1] + g.e) bwt = 0.0;
+        if (bwt != 0.0 && ncand[a] < 2) { cand[a][ncand[a]] = part; wt[a][ncand[a]] = bwt; ncand[a]++; }
+      }
+      wts_n *= ncand[a];
+    }
+    z64 acc = mk<double>(0, 0);
+    for (int i0 = 0; i0 < ncand[0]; ++i0)
+      for (int i1 = 0; i1 < ncand[1]; ++i1)
+        for (int i2 = 0; i2 < ncand[2]; ++i2) {
+          int part[3] = {cand[0][i0], cand[1][i1], cand[2][i2]};
+          int sid = (part[2] * g.parts[1] + part[1]) * g.parts[0] + part[0];
+          const SubDesc& s = g.subs[sid];
+          int xl[3] = {xg[0] - s.lo[0], xg[1] - s.lo[1], g.dim == 3 ? xg[2] - s.lo[2] : 0};
+          cplx<T> v = U[(long long)r * g.ltotal + s.vofs + flat(xl, s.ext)];
+          double bw = wt[0][i0] * wt[1][i1] * wt[2][i2];
+          acc = acc + bw * mk<double>((double)v.x, (double)v.y);
+        }
+    w[i] = acc;
+    (void)wts_n;
+  }
+}
+
+cudaError_t launch_assemble(ddm_ctx* c, const void* U, z64* w, int nrhs) {
+  if (c->prec == DDM_MIXED)
+    k_assemble<float><<<1216, 256, 0, c->st>>>(c->g, (const c32*)U, w, nrhs);
+  else
+    k_assemble<double><<<1216, 256, 0, c->st>>>(c->g, (const z64*)U, w, nrhs);
+  return cudaGetLastError();
+}
+
+}  // namespace ddm

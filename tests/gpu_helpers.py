@@ -1,0 +1,30 @@
+"""Helpers shared by the GPU tests: oracle construction and local-layout conversion."""
+import numpy as np
+
+from oracle.ddm import DDMOracle
+
+
+def oracle_of(wl, workers=1):
+    return DDMOracle(wl.n, wl.h, wl.cuts, wl.ov, wl.npml, wl.sigma0, wl.power, wl.omega, wl.c, workers=workers)
+
+
+def to_local(o, per_sub, dtype=np.complex128):
+    """Concatenate per-subdomain arrays in the library's local layout (subdomains in C order of
+    their index, each x-fastest), which is the oracle's subdomain order and array order."""
+    return np.concatenate([np.asarray(per_sub[R], dtype=dtype).ravel() for R in o.subs])
+
+
+def from_local(o, flat):
+    out, ofs = {}, 0
+    for R in o.subs:
+        n = int(np.prod(o.sub_shape[R]))
+        out[R] = np.asarray(flat[ofs: ofs + n]).reshape(o.sub_shape[R])
+        ofs += n
+    return out
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)

@@ -1,0 +1,53 @@
+"""CPU-side checks of the C-ABI library: it builds, loads and exports every declared symbol.
+No compute call runs here (there is no GPU in this environment)."""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1807_04180_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_header_symbol(built):
+    from paper_1807_04180_gb300 import ddm
+    names = ddm.header_symbols()
+    assert {"ddm_setup", "ddm_factor", "ddm_apply", "ddm_solve", "ddm_destroy", "ddm_last_error"} <= set(names)
+    L = ctypes.CDLL(built)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding wraps every declared entry point under the same name
+    assert all(hasattr(ddm, n) for n in names)
+
+
+def test_setup_rejects_bad_params_before_touching_the_gpu(built):
+    """Parameter validation happens before any CUDA call, so it can be exercised here."""
+    from paper_1807_04180_gb300 import ddm, workloads as W
+    wl = W.tiny_2d()
+    p, keep = ddm.params_from(wl)
+    p.dim = 4
+    out = ctypes.c_void_p()
+    L = ddm.lib()
+    st = L.ddm_setup(ctypes.byref(p), 1.0, ctypes.c_void_p(16), None, ctypes.byref(out))
+    assert st == ddm.DDM_E_INVAL and b"dim" in L.ddm_last_error(None)
+    p, keep = ddm.params_from(wl)
+    p.overlap = 0
+    st = L.ddm_setup(ctypes.byref(p), 1.0, ctypes.c_void_p(16), None, ctypes.byref(out))
+    assert st == ddm.DDM_E_INVAL
+    p, keep = ddm.params_from(wl)
+    st = L.ddm_setup(ctypes.byref(p), -1.0, ctypes.c_void_p(16), None, ctypes.byref(out))
+    assert st == ddm.DDM_E_INVAL
+    # a part narrower than twice the overlap is refused
+    wl2 = W.tiny_2d(n=12, parts=(4, 4), ov=2)
+    p, keep = ddm.params_from(wl2)
+    st = L.ddm_setup(ctypes.byref(p), 1.0, ctypes.c_void_p(16), None, ctypes.byref(out))
+    assert st == ddm.DDM_E_INVAL
+
+
+def test_binding_refuses_cpu_tensors(built):
+    torch = pytest.importorskip("torch")
+    from paper_1807_04180_gb300 import ddm
+    with pytest.raises(TypeError):
+        ddm._ptr(torch.zeros(4, dtype=torch.complex128))

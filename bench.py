@@ -1,0 +1,411 @@
+"""Benchmark of the GB300 overlapping-DDM Helmholtz solver.
+
+Default workload: 2D heterogeneous medium, 1024^2 interior (1048^2 with the 12-cell overlap +
+PML band), c in [1.5, 4.5] as a seeded sum of 20 Gaussians, 10 points per wavelength at
+c_min, 16x16 subdomains, one single-shot source, complex64 local factors/solves inside FP64
+FGMRES(60) preconditioned by K = 2 DDM steps, tolerance 1e-6.
+
+One step = the whole hot path for one problem instance: assemble the medium (k^2), factor
+all 256 subdomain operators, and solve to a relative residual of 1e-6 (FGMRES, DDM steps,
+transfers, global operator, Arnoldi), with the inputs already in HBM.  `value` is solves
+per second over all ranks; `ms_per_step` is the time to solution including factorisation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the method has no data-path
+exchange across GPUs here); the timed region is bracketed by barriers and the maximum over
+ranks is taken.  The reference arm times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1807_04180_gb300 import workloads as W  # noqa: E402
+
+METRIC = "time-to-1e-6 solve throughput, 2D heterogeneous 1024^2 DDM-FGMRES (16x16 subdomains)"
+UNIT = "solve/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_heterogeneous-1024.json")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# ----------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1807_04180_gb300 import ddm as D
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = W.heterogeneous_2d()
+    prec = D.DDM_MIXED if args.precision == "mixed" else D.DDM_FP64
+    mode = D.DDM_FGMRES if args.mode == "fgmres" else D.DDM_STEPPING
+    s = D.Solver(wl, precision=prec, max_rhs=1, device=str(dev))
+    ctx = s.ctx
+    c_dev = s.c
+    f_dev = s.to_dev(wl.f[0])
+    u_dev = torch.zeros(wl.c.shape, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
+    info_last = {}
+
+    def step():
+        D.ddm_set_medium(ctx, wl.omega, c_dev)
+        D.ddm_factor(ctx)
+        info = D.ddm_solve(ctx, f_dev, u_dev, tol=wl.tol, max_it=args.max_it, mode=mode, K=args.K,
+                           restart=args.restart)
+        info_last.update(info)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    D.ddm_timing(ctx, enable=True, reset=True)
+    D.ddm_kernel_launches(ctx, reset=True)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    dev_ms = e0.elapsed_time(e1)
+    # the library synchronises inside ddm_solve (convergence checks), so device events and
+    # host wall time agree; take the larger
+    elapsed_ms = max(dev_ms, wall * 1e3)
+    tms = D.ddm_timing(ctx, enable=False)
+    launches = D.ddm_kernel_launches(ctx)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    # dominant kernel: the batched local solves (k_solve2d)
+    solve_ms, solve_n = tms["solve"]
+    per_solve_bytes, stored = D.ddm_factor_bytes(ctx)
+    lay = D.ddm_local_layout(ctx)
+    el = 8 if prec == D.DDM_MIXED else 16
+    vec_bytes = 6 * lay["total"] * el          # src read, t write/read, x write, U read+write
+    launch_bytes = per_solve_bytes + vec_bytes
+    avg_launch_ms = solve_ms / max(solve_n, 1)
+    achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9
+    pk = peaks()
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "solve2d_traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as fh:
+            tr = json.load(fh)
+        if tr.get("precision") == args.precision and tr.get("kernel_rev") == KERNEL_REV:
+            traffic = tr.get("bytes_per_launch")
+    out = {
+        "metric": METRIC, "value": world * 1e3 / ms_per_step, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 local / c128 krylov" if prec == D.DDM_MIXED else "c128",
+        "data": "synthetic",
+        "config": {"workload": wl.name + " (2D heterogeneous, c in [1.5,4.5] sum of 20 seeded Gaussians, "
+                   "10 ppw at c_min, single-shot source)",
+                   "grid": "1024^2 interior + 12-cell overlap/PML band (1048^2)", "subdomains": "16x16 of 64^2 (+2 ov +10 pml)",
+                   "precision": args.precision, "mode": args.mode, "K": args.K, "restart": args.restart,
+                   "tol": wl.tol, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 ({stored / 1e9:.2f} GB of factors streamed per sweep)"},
+        "time_to_solution_ms": info_last.get("solve_ms"), "factor_ms": info_last.get("factor_ms"),
+        "fgmres_iters": info_last.get("iters"), "ddm_steps": info_last.get("ddm_steps"),
+        "rel_residual": info_last.get("rel_residual"), "n_unique_factors": info_last.get("n_unique_factors"),
+        "roofline": {"bound": "hbm", "kernel": "k_solve2d (batched block-tridiagonal local solves)",
+                     "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"],
+                     "traffic": traffic, "algorithmic_bytes_per_launch": launch_bytes,
+                     "avg_launch_ms": avg_launch_ms, "launches": solve_n},
+        "kernel_ms": {k: v[0] / args.steps for k, v in tms.items()},
+        "gpu_launches": launches, "clocks": ck,
+    }
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    c_h = torch.from_numpy(np.ascontiguousarray(wl.c)).pin_memory()
+    f_h = torch.from_numpy(np.ascontiguousarray(wl.f[0])).pin_memory()
+    u_h = torch.zeros(wl.c.shape, dtype=torch.complex128).pin_memory()
+
+    def e2e_step():
+        D.ddm_set_medium_host(ctx, wl.omega, c_h)
+        D.ddm_factor(ctx)
+        D.ddm_solve_host(ctx, f_h, u_h, tol=wl.tol, max_it=args.max_it, mode=mode, K=args.K, restart=args.restart)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    n_e2e = max(1, min(args.steps, 5))
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    out["e2e"] = {"value": world * 1e3 / e2e_ms, "unit": UNIT,
+                  "h2d_bytes_per_step": int(c_h.numel() * 8 + f_h.numel() * 16),
+                  "d2h_bytes_per_step": int(u_h.numel() * 16)}
+    # FP64 GPU DDM on the same problem, for the mixed-precision speedup
+    if rank == 0 and args.precision == "mixed" and not args.no_fp64_compare:
+        s64 = D.Solver(wl, precision=D.DDM_FP64, max_rhs=1, device=str(dev))
+        u64 = torch.zeros_like(u_dev)
+        D.ddm_factor(s64.ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D.ddm_factor(s64.ctx)
+        i64 = D.ddm_solve(s64.ctx, f_dev, u64, tol=wl.tol, max_it=args.max_it, mode=mode, K=args.K,
+                          restart=args.restart)
+        torch.cuda.synchronize()
+        t64 = (time.perf_counter() - t0) * 1e3
+        diff = float(torch.linalg.vector_norm(u64 - u_dev) / torch.linalg.vector_norm(u64))
+        out["fp64_gpu"] = {"ms_per_step": t64, "time_to_solution_ms": i64["solve_ms"], "factor_ms": i64["factor_ms"],
+                           "fgmres_iters": i64["iters"], "speedup_of_mixed": t64 / ms_per_step,
+                           "rel_diff_mixed_vs_fp64": diff}
+        s64.close()
+    # agreement with the FP64 oracle at the stored sample nodes (written by the oracle only)
+    if rank == 0 and os.path.exists(GOLDEN):
+        with open(GOLDEN) as fh:
+            gold = json.load(fh)
+        idx = torch.as_tensor(gold["sample_index"], device=dev)
+        got = u_dev.reshape(-1)[idx].cpu().numpy()
+        ref = np.array(gold["sample_re"]) + 1j * np.array(gold["sample_im"])
+        out["oracle_sample_rel_err"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        out["oracle_fgmres_iters_to_1e-6"] = gold["fgmres_iters_to_1e-6"]
+    s.close()
+    return out
+
+
+KERNEL_REV = "solve2d-v2"
+
+
+def profile_kernels(args):
+    """Small profiling case on the bench workload: medium assembly, factorisation and one
+    preconditioner application with K = 4 (4 batched local solves, 3 transfers), repeated
+    warmup + steps times.  Holds about 1.5 GB on the device."""
+    import torch
+    from paper_1807_04180_gb300 import ddm as D
+    wl = W.heterogeneous_2d()
+    prec = D.DDM_MIXED if args.precision == "mixed" else D.DDM_FP64
+    s = D.Solver(wl, precision=prec, max_rhs=1)
+    b = torch.zeros(wl.c.shape, dtype=torch.complex128, device="cuda")
+    D.ddm_rhs(s.ctx, s.to_dev(wl.f[0]), b)
+    w = torch.zeros_like(b)
+    for _ in range(args.warmup + args.steps):
+        D.ddm_set_medium(s.ctx, wl.omega, s.c)
+        D.ddm_factor(s.ctx)
+        D.ddm_apply(s.ctx, 4, b, w)
+    torch.cuda.synchronize()
+    s.close()
+
+
+# ----------------------------------------------------------------------------------- oracle
+def oracle_sample(budget_s, workers):
+    """Time the FP64 oracle on a bounded sample of the workload and extrapolate one solve.
+
+    The sample: factor S of the 256 subdomains (SuperLU), then for the same S subdomains one
+    DDM step (transfers into them and their local solves), one global operator application
+    and one classical Gram-Schmidt pass against j = restart/2 vectors.  A full solve is
+    (256/S) x factor + n_it x [K x (256/S) x step + A + 2 CGS passes], with n_it the oracle's
+    own FGMRES iteration count to 1e-6 on this workload (tests/golden, written by the oracle).
+    """
+    from oracle.ddm import DDMOracle
+    wl = W.heterogeneous_2d()
+    o = DDMOracle(wl.n, wl.h, wl.cuts, wl.ov, wl.npml, wl.sigma0, wl.power, wl.omega, wl.c, workers=workers)
+    nsub = len(o.subs)
+    if os.path.exists(GOLDEN):
+        with open(GOLDEN) as fh:
+            n_it = json.load(fh)["fgmres_iters_to_1e-6"]
+        it_src = "oracle FGMRES iteration count (tests/golden)"
+    else:
+        n_it = 60
+        it_src = "assumed 60 iterations (no oracle record)"
+    from concurrent.futures import ThreadPoolExecutor
+    import scipy.sparse.linalg as spla
+    # size the sample to the budget: about 0.09 s of factor + step work per subdomain per worker
+    S = int(max(8, min(nsub, budget_s * max(1, workers) / 0.12)))
+    S = min(nsub, S)
+    rng = np.random.default_rng(0)
+    sample = [o.subs[i] for i in sorted(rng.choice(nsub, S, replace=False))]
+    b = o.rhs(wl.f[0])
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max(1, workers)) as ex:
+        lus = list(ex.map(lambda R: spla.splu(o.sub_A[R].tocsc()), sample))
+    for R, lu in zip(sample, lus):
+        o.sub_lu[R] = lu
+    t_fac = time.perf_counter() - t0
+    # one step on the sample: step-1 sources for all of them, then transfers + solves
+    hist = {1: {R: o.local_solve(R, o.restrict_own(R, b)) if R in o.sub_lu else np.zeros(o.sub_shape[R], complex)
+                for R in o.subs}}
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max(1, workers)) as ex:
+        list(ex.map(lambda R: o.local_solve(R, o.step_source(R, 2, hist)), sample))
+    t_step = time.perf_counter() - t0
+    x = (np.random.default_rng(1).standard_normal(o.gshape) + 0j)
+    t0 = time.perf_counter()
+    o.apply_global(x)
+    t_A = time.perf_counter() - t0
+    j = max(1, wl.restart // 2)
+    V = np.zeros((j, x.size), dtype=np.complex128)
+    w = x.ravel().copy()
+    t0 = time.perf_counter()
+    c = V.conj() @ w
+    w = w - V.T @ c
+    t_cgs = time.perf_counter() - t0
+    est = t_fac * nsub / S + n_it * (wl.K * t_step * nsub / S + t_A + 2 * t_cgs)
+    return {"est_s": est, "sample": f"{S}/{nsub} subdomains: factor + one DDM step (transfer + solve), one global "
+                                    f"A x, one CGS pass at j={j}; scaled to {n_it} FGMRES iterations x K={wl.K} "
+                                    f"({it_src})", "cores": max(1, workers)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    workers = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    budget = max(2.0, 150.0 / (args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(budget, workers)
+    ests = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle_sample(budget, workers)
+        ests.append(r["est_s"])
+    wall = time.perf_counter() - t0
+    est = statistics.mean(ests)
+    value = 1.0 / est
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "2d-heterogeneous-1024 (same seeded inputs)", "K": 2, "restart": 60, "tol": 1e-6},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": wall / args.steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--mode", choices=["fgmres", "stepping"], default="fgmres")
+    ap.add_argument("--K", type=int, default=2)
+    ap.add_argument("--restart", type=int, default=60)
+    ap.add_argument("--max-it", type=int, default=600)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="profiling case for ncu: assemble, factor and K=4 DDM steps (no Krylov workspace), no JSON")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    args.warmup = max(args.warmup, 3)
+    if args.profile_kernels:
+        profile_kernels(args)
+        return
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            workers = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 1
+            r = oracle_sample(15.0, workers)
+            out["cpu_baseline"] = {"value": 1.0 / r["est_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                   "sample": r["sample"]}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -104,6 +104,17 @@ typedef struct {
  * Does not factor.  Errors: DDM_E_INVAL, DDM_E_NOMEM, DDM_E_CUDA.           */
 ddm_status ddm_setup(const ddm_params *p, double omega, const double *c_dev, void *stream, ddm_ctx **out);
 
+/* Replace the medium: recompute k^2 = (omega / c)^2 from c_dev (float64, global
+ * extended grid, device) on the context's stream (the assembly step of the
+ * path) and mark the context unfactored; call ddm_factor before solving.
+ * Errors: DDM_E_INVAL, DDM_E_CUDA.                                          */
+ddm_status ddm_set_medium(ddm_ctx *ctx, double omega, const double *c_dev);
+
+/* ddm_set_medium with the wave speed in host memory (float64, global
+ * extended grid): copied to a library-owned device buffer on the context's
+ * stream, then as ddm_set_medium.                                            */
+ddm_status ddm_set_medium_host(ddm_ctx *ctx, double omega, const double *c_host);
+
 /* Factor every distinct subdomain operator (Algorithm 3.1's local problems;
  * the paper uses a sparse direct solver).  Subdomains whose extended grids
  * carry identical operators share one factor.  Each factor is the block
@@ -193,6 +204,10 @@ ddm_status ddm_steps(ddm_ctx *ctx, const void *b_dev, int nsteps, void *w_dev, v
  * out_launches[i] the matching launch counts (either array may be NULL).
  * enable != 0 turns recording on, 0 off; reset clears the sums.            */
 ddm_status ddm_timing(ddm_ctx *ctx, int enable, int reset, double *out_ms, int64_t *out_launches);
+
+/* Number of kernels this context has launched (since creation or the last
+ * reset); reset != 0 clears the counter after reading it.                    */
+ddm_status ddm_kernel_launches(ddm_ctx *ctx, int64_t *count, int reset);
 
 /* Bytes of subdomain factors read by one batched local solve of one
  * right-hand side per subdomain (each distinct factor streamed twice, once

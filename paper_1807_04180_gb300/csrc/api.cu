@@ -206,6 +206,8 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
   ddm_status st = DDM_OK;
   auto body = [&]() -> ddm_status {
     ALLOC(c->d_k2, sizeof(double) * g.nglob);
+    ALLOC(c->d_lcoef, le * g.ltotal * (2 * d + 1));
+    ALLOC(c->d_gcoef, sizeof(z64) * g.nglob * (2 * d + 1));
     ALLOC(c->d_tab, sizeof(z64) * tab_total);
     ALLOC(c->d_beta, sizeof(double) * (ov + 1));
     ALLOC(c->d_owner, sizeof(int) * owner.size());
@@ -228,10 +230,12 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     CK(cudaMemcpyAsync(c->d_cuts, cutsv.data(), sizeof(int) * cutsv.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDesc) * g.nsub, cudaMemcpyHostToDevice, c->st));
     g.k2 = c->d_k2; g.tab = c->d_tab; g.beta = c->d_beta; g.subs = c->d_subs;
+    g.lcoef = c->d_lcoef; g.gcoef = c->d_gcoef;
     for (int a = 0; a < 3; ++a) { g.owner[a] = c->d_owner + own_ofs[a]; g.cuts[a] = c->d_cuts + cut_ofs[a]; }
     CK(launch_build_tables(c, d_tdesc, (int)(tdesc.size() / 3), p->sigma0, p->pml_power, p->pml));
     CK(launch_k2(c, c_dev));
     CK(launch_beta(c));
+    CK(launch_coefs(c));
     CK(cudaStreamSynchronize(c->st));
     return DDM_OK;
   };
@@ -249,9 +253,9 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
 extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (!c) return DDM_OK;
   if (c->st || true) cudaStreamSynchronize(c->st);
-  void* ptrs[] = {c->d_subs, c->d_k2, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
+  void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
-                  c->d_gr, c->d_gw, c->d_hostbuf, c->d_V, c->d_Z, c->d_H, c->d_gs};
+                  c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_V, c->d_Z, c->d_H, c->d_gs};
   for (void* q : ptrs) if (q) cudaFree(q);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -261,6 +265,31 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
 }
 
 extern "C" const char* ddm_last_error(const ddm_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
+
+extern "C" ddm_status ddm_set_medium(ddm_ctx* c, double omega, const double* c_dev) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (!(omega > 0) || !c_dev) return fail(c, DDM_E_INVAL, "omega must be > 0 and c_dev non-null");
+  c->omega = omega;
+  CK(launch_k2(c, c_dev));
+  CK(launch_coefs(c));
+  c->factored = false;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_set_medium_host(ddm_ctx* c, double omega, const double* c_host) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (!c_host) return fail(c, DDM_E_INVAL, "c_host is null");
+  if (!c->d_chost) CK(cudaMalloc((void**)&c->d_chost, sizeof(double) * c->g.nglob));
+  CK(cudaMemcpyAsync(c->d_chost, c_host, sizeof(double) * c->g.nglob, cudaMemcpyHostToDevice, c->st));
+  return ddm_set_medium(c, omega, c->d_chost);
+}
+
+extern "C" ddm_status ddm_kernel_launches(ddm_ctx* c, int64_t* count, int reset) {
+  if (!c) return DDM_E_INVAL;
+  if (count) *count = c->nlaunch;
+  if (reset) c->nlaunch = 0;
+  return DDM_OK;
+}
 
 // =====================================================================================
 // factorisation

@@ -80,6 +80,8 @@ struct Geom {
   int gtab[MAXDIM];       // offsets of the global box's tables
   const double* beta;     // beta_0(q / ov), q = 0..ov (beta[ov] = 0)
   const SubDesc* subs;
+  const void* lcoef;      // per-subdomain operator planes (local precision)
+  const z64* gcoef;       // global operator planes (FP64)
   const int* owner[MAXDIM];  // part owning global extended index g along axis a
   const int* cuts[MAXDIM];   // parts+1 cuts per axis
   int parts[MAXDIM];
@@ -141,6 +143,8 @@ struct ddm_ctx {
   ddm::SubDesc* d_subs = nullptr;
   // device arrays
   double* d_k2 = nullptr;
+  void* d_lcoef = nullptr;       // per-subdomain operator planes (local precision), ltotal x (2 dim + 1)
+  ddm::z64* d_gcoef = nullptr;   // global operator planes (FP64), nglob x (2 dim + 1)
   ddm::z64* d_tab = nullptr;
   double* d_beta = nullptr;
   int* d_owner = nullptr;
@@ -167,12 +171,15 @@ struct ddm_ctx {
   ddm::z64* d_gr = nullptr;      // max_rhs wide
   ddm::z64* d_gw = nullptr;      // max_rhs wide
   ddm::z64* d_hostbuf = nullptr; // staging for ddm_solve_host: f then u, max_rhs wide each
+  double* d_chost = nullptr;     // staging for ddm_set_medium_host
   // Krylov workspace (allocated on first FGMRES solve)
   int kry_m = 0;
   ddm::z64* d_V = nullptr;
   ddm::z64* d_Z = nullptr;
   ddm::z64* d_H = nullptr;       // (m+1) x m column major
   ddm::z64* d_gs = nullptr;      // Givens: cs[m], sn[m], g[m+1], y[m]
+  // kernels launched by this context (ddm_kernel_launches)
+  long long nlaunch = 0;
   // timing
   bool timing = false;
   double t_ms[ddm::T_NSLOT] = {0};
@@ -186,6 +193,7 @@ namespace ddm {
 // launchers implemented in the .cu files (all enqueue on ctx->st)
 cudaError_t launch_build_tables(ddm_ctx* c, const int* d_tdesc, int ntab, double sigma0, double power, int npml);
 cudaError_t launch_k2(ddm_ctx* c, const double* c_dev);
+cudaError_t launch_coefs(ddm_ctx* c);
 cudaError_t launch_beta(ddm_ctx* c);
 cudaError_t launch_sub_hash(ddm_ctx* c, unsigned long long* d_hash);
 cudaError_t launch_sub_compare(ddm_ctx* c, const int* d_pairs, int npairs, int* d_mismatch);

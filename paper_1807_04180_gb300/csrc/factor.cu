@@ -4,7 +4,7 @@
 // x-lines: diagonal blocks T_k (tridiagonal, x-couplings of line k) and diagonal
 // off-diagonal blocks L_k = diag(c_S(., k)), U_k = diag(c_N(., k)).  Block elimination
 // gives D_0 = T_0, D_k = T_k - L_k D_{k-1}^{-1} U_{k-1}; the factor stores
-// G_k = D_k^{-1} (dense b x b, row-major, leading dimension ldb), inverted in shared memory
+// G_k = D_k^{-1} (dense b x b, column-major, leading dimension ldb), inverted in shared memory
 // by Gauss-Jordan elimination with partial (row) pivoting inside the block.  One CTA per
 // distinct factor walks the lines sequentially.
 #include <algorithm>
@@ -21,8 +21,9 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
   const long long fofs = fofs_arr[blockIdx.x];
   const int ldb = ldbs[blockIdx.x];
   const int b = s.ext[0], m = s.ext[1];
-  cplx<T>* M = (cplx<T>*)smem;               // b x ldb working block
-  cplx<T>* colp = M + (long long)b * ldb;    // column p multipliers
+  const int ldm = b | 1;                     // odd leading dimension: conflict-free column access
+  cplx<T>* M = (cplx<T>*)smem;               // b x ldm working block
+  cplx<T>* colp = M + (long long)b * ldm;    // column p multipliers
   cplx<T>* cC = colp + b;                    // centre of line k
   cplx<T>* cE = cC + b;                      // x+ coupling
   cplx<T>* cW = cE + b;                      // x- coupling
@@ -40,38 +41,36 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
   __syncthreads();
 
   for (int k = 0; k < m; ++k) {
-    // coefficients of line k (FP64 evaluation, cast to T)
-    for (int i = tid; i < b; i += nth) {
-      int x[3] = {i, k, 0};
-      long long gi = (long long)(s.lo[1] + k) * g.N[0] + (s.lo[0] + i);
-      Coef cf = coef_at(g, s.tab, s.ext, x, g.k2[gi]);
-      cC[i] = ccast<T>(cf.c); cE[i] = ccast<T>(cf.p[0]); cW[i] = ccast<T>(cf.m[0]);
-      cS[i] = ccast<T>(cf.m[1]); cNn[i] = ccast<T>(cf.p[1]);
+    // coefficients of line k from the operator planes (C, W, E, S, N)
+    {
+      const long long len = (long long)b * m;
+      const cplx<T>* lc = (const cplx<T>*)g.lcoef + s.vofs * 5 + (long long)k * b;
+      for (int i = tid; i < b; i += nth) {
+        cC[i] = lc[i]; cW[i] = lc[len + i]; cE[i] = lc[2 * len + i];
+        cS[i] = lc[3 * len + i]; cNn[i] = lc[4 * len + i];
+      }
     }
     __syncthreads();
-    // D_k = T_k - L_k G_{k-1} U_{k-1}; rows are rebuilt warp-wise (read the whole row of
-    // G_{k-1} through the column map first, then overwrite), and G_{k-1} is written out.
+    // D_k = T_k - L_k G_{k-1} U_{k-1}; each warp rebuilds whole rows (reading the row of
+    // G_{k-1} through the column map into registers first, then overwriting it)
     for (int i = warp; i < b; i += nwarp) {
       cplx<T> v[4];
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
         int j = lane + 32 * jj;
-        v[jj] = (k > 0 && j < b) ? M[(long long)i * ldb + cm[j]] : mk<T>(0, 0);
+        v[jj] = (k > 0 && j < b) ? M[i * ldm + cm[j]] : mk<T>(0, 0);
       }
       __syncwarp();
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) {
         int j = lane + 32 * jj;
         if (j < b) {
-          if (k > 0) Gout[fofs + ((long long)(k - 1) * b + i) * ldb + j] = v[jj];
           cplx<T> d = mk<T>(0, 0);
           if (k > 0) d = -(cS[i] * v[jj] * cNp[j]);
           if (j == i) d = d + cC[i];
           if (j == i + 1) d = d + cE[i];
           if (j == i - 1) d = d + cW[i];
-          M[(long long)i * ldb + j] = d;
-        } else if (j < ldb && k > 0) {
-          Gout[fofs + ((long long)(k - 1) * b + i) * ldb + j] = mk<T>(0, 0);
+          M[i * ldm + j] = d;
         }
       }
     }
@@ -83,7 +82,7 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
       if (warp == 0) {
         T best = (T)-1; int bi = p;
         for (int i = p + lane; i < b; i += 32) {
-          T a = cabs2(M[(long long)i * ldb + p]);
+          T a = cabs2(M[i * ldm + p]);
           if (a > best) { best = a; bi = i; }
         }
         for (int o = 16; o; o >>= 1) {
@@ -93,7 +92,7 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
         }
         if (lane == 0) {
           s_piv = bi;
-          cplx<T> pv = M[(long long)bi * ldb + p];
+          cplx<T> pv = M[bi * ldm + p];
           if (!(best > (T)0) || !isfinite(best)) { s_bad = 1; s_inv = mk<T>(0, 0); }
           else s_inv = cinv(pv);
           perm[p] = bi;
@@ -105,48 +104,64 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
       // phase A: read row p, row r and column p (after the interchange)
       cplx<T> ap = mk<T>(0, 0), ar = mk<T>(0, 0), cpv = mk<T>(0, 0);
       if (tid < b) {
-        ap = M[(long long)p * ldb + tid];
-        ar = M[(long long)r * ldb + tid];
+        ap = M[p * ldm + tid];
+        ar = M[r * ldm + tid];
         int i = tid;
-        cpv = (i == p) ? mk<T>(0, 0) : (i == r ? M[(long long)p * ldb + p] : M[(long long)i * ldb + p]);
+        cpv = (i == p) ? mk<T>(0, 0) : (i == r ? M[p * ldm + p] : M[i * ldm + p]);
       }
       __syncthreads();
       // phase B: interchange, scale the pivot row, keep the multipliers
       if (tid < b) {
         int j = tid;
-        cplx<T> nr = (j == p) ? inv : ar * inv;
-        M[(long long)p * ldb + j] = nr;
-        if (r != p) M[(long long)r * ldb + j] = ap;
+        M[p * ldm + j] = (j == p) ? inv : ar * inv;
+        if (r != p) M[r * ldm + j] = ap;
         colp[j] = cpv;
       }
       __syncthreads();
-      // phase C: eliminate column p from every other row
-      for (int idx = tid; idx < b * b; idx += nth) {
-        int i = idx / b, j = idx - i * b;
-        if (i == p) continue;
-        cplx<T> mp = M[(long long)p * ldb + j];
-        cplx<T> cur = (j == p) ? mk<T>(0, 0) : M[(long long)i * ldb + j];
-        M[(long long)i * ldb + j] = cur - colp[i] * mp;
+      // phase C: eliminate column p from every other row (warp per row set, lanes over columns,
+      // the pivot row held in registers)
+      {
+        cplx<T> mp[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          int j = lane + 32 * jj;
+          mp[jj] = j < b ? M[p * ldm + j] : mk<T>(0, 0);
+        }
+        for (int i = warp; i < b; i += nwarp) {
+          if (i == p) continue;
+          const cplx<T> f = colp[i];
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            int j = lane + 32 * jj;
+            if (j < b) {
+              cplx<T> cur = (j == p) ? mk<T>(0, 0) : M[i * ldm + j];
+              cfma(cur, -f, mp[jj]);
+              M[i * ldm + j] = cur;
+            }
+          }
+        }
       }
       __syncthreads();
     }
-    // column map undoing the interchanges (applied when the block is read)
+    // column map undoing the interchanges
     if (tid == 0) {
       for (int j = 0; j < b; ++j) cm[j] = j;
       for (int p = b - 1; p >= 0; --p) { int q = perm[p]; int t = cm[p]; cm[p] = cm[q]; cm[q] = t; }
     }
     __syncthreads();
+    // write G_k transposed (column j of G_k contiguous: element (i, j) at (k b + j) ldb + i)
+    for (int idx = tid; idx < b * ldb; idx += nth) {
+      const int j = idx / ldb, i = idx - j * ldb;
+      Gout[fofs + ((long long)k * b + j) * ldb + i] = i < b ? M[i * ldm + cm[j]] : mk<T>(0, 0);
+    }
   }
-  // write the last block
-  for (int i = warp; i < b; i += nwarp)
-    for (int j = lane; j < ldb; j += 32)
-      Gout[fofs + ((long long)(m - 1) * b + i) * ldb + j] = (j < b) ? M[(long long)i * ldb + cm[j]] : mk<T>(0, 0);
   if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
 }
 
 size_t factor_smem_bytes(int b, int ldb, int prec) {
   size_t el = prec == DDM_MIXED ? sizeof(c32) : sizeof(z64);
-  return (size_t)b * ldb * el + 7 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
+  (void)ldb;
+  return (size_t)b * (b | 1) * el + 7 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
 }
 
 // All distinct factors in one launch, one CTA each.  d_reps[f] is a subdomain using factor
@@ -158,10 +173,12 @@ cudaError_t launch_factor_all(ddm_ctx* c, const int* d_reps, const long long* d_
   if (c->prec == DDM_MIXED) {
     e = cudaFuncSetAttribute(k_factor2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    ++c->nlaunch;
     k_factor2d<float><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
   } else {
     e = cudaFuncSetAttribute(k_factor2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    ++c->nlaunch;
     k_factor2d<double><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (z64*)c->d_G, c->d_err);
   }
   return cudaGetLastError();

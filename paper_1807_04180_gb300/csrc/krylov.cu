@@ -11,13 +11,12 @@ __global__ void k_global_apply(Geom g, const z64* x, z64* y, const z64* bsub, in
     long long gi = i % n;
     long long base = i - gi;
     int xg[3] = {(int)(gi % g.N[0]), (int)((gi / g.N[0]) % g.N[1]), (int)(gi / ((long long)g.N[0] * g.N[1]))};
-    Coef cf = coef_at(g, g.gtab, g.N, xg, g.k2[gi]);
     z64 acc = mk<double>(0, 0);
-    cfma(acc, cf.c, x[i]);
+    cfma(acc, g.gcoef[gi], x[i]);
     long long stride = 1;
     for (int a = 0; a < g.dim; ++a) {
-      if (xg[a] + 1 < g.N[a]) cfma(acc, cf.p[a], x[base + gi + stride]);
-      if (xg[a] > 0) cfma(acc, cf.m[a], x[base + gi - stride]);
+      if (xg[a] + 1 < g.N[a]) cfma(acc, g.gcoef[(2 + 2 * a) * n + gi], x[base + gi + stride]);
+      if (xg[a] > 0) cfma(acc, g.gcoef[(1 + 2 * a) * n + gi], x[base + gi - stride]);
       stride *= g.N[a];
     }
     y[i] = bsub ? bsub[i] - acc : acc;
@@ -25,6 +24,7 @@ __global__ void k_global_apply(Geom g, const z64* x, z64* y, const z64* bsub, in
 }
 
 cudaError_t launch_global_apply(ddm_ctx* c, const z64* x, z64* y, const z64* bsub, int nrhs) {
+  ++c->nlaunch;
   k_global_apply<<<1216, 256, 0, c->st>>>(c->g, x, y, bsub, nrhs);
   return cudaGetLastError();
 }
@@ -59,6 +59,7 @@ __global__ void k_norm2_partial(const z64* x, long long n, int nvec, double* par
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 
 cudaError_t launch_norm2_partial(ddm_ctx* c, const z64* x, long long n, int nvec, double* part, int* nblocks) {
+  ++c->nlaunch;
   k_norm2_partial<<<RED_BLOCKS, 256, 0, c->st>>>(x, n, nvec, part);
   *nblocks = RED_BLOCKS;
   return cudaGetLastError();
@@ -75,6 +76,7 @@ __global__ void k_sum_partials(const double* part, int nblocks, int nvals, doubl
 }
 
 cudaError_t launch_sum_partials(ddm_ctx* c, const double* part, int nblocks, int nvals, double* out) {
+  ++c->nlaunch;
   k_sum_partials<<<nvals, 256, 0, c->st>>>(part, nblocks, nvals, out);
   return cudaGetLastError();
 }
@@ -108,6 +110,7 @@ __global__ void k_dots(const z64* V, int nv0, int nv, const z64* w, long long n,
 cudaError_t launch_dots(ddm_ctx* c, const z64* V, int nv, const z64* w, long long n, double* part, int* nblocks) {
   for (int v0 = 0; v0 < nv; v0 += 8) {
     int cnt = min(8, nv - v0);
+    ++c->nlaunch;
     k_dots<8><<<RED_BLOCKS, 256, 0, c->st>>>(V, v0, cnt, w, n, part, nv);
   }
   *nblocks = RED_BLOCKS;
@@ -133,6 +136,7 @@ __global__ void k_arnoldi_coef(const double* part, int nblocks, int nv, z64* Hco
 }
 
 cudaError_t launch_arnoldi_coef(ddm_ctx* c, const double* part, int nblocks, int nv, z64* Hcol, z64* coef, int first) {
+  ++c->nlaunch;
   k_arnoldi_coef<<<nv, 256, 0, c->st>>>(part, nblocks, nv, Hcol, coef, first);
   return cudaGetLastError();
 }
@@ -153,6 +157,7 @@ __global__ void k_sub_axpy(const z64* V, int nv, const z64* coef, z64* w, long l
 }
 
 cudaError_t launch_sub_axpy(ddm_ctx* c, const z64* V, int nv, const z64* coef, z64* w, long long n) {
+  ++c->nlaunch;
   k_sub_axpy<<<RED_BLOCKS * 2, 256, 0, c->st>>>(V, nv, coef, w, n);
   return cudaGetLastError();
 }
@@ -197,6 +202,7 @@ __global__ void k_givens(int j, int m, const double* nrm2, z64* H, z64* gs, doub
 }
 
 cudaError_t launch_givens(ddm_ctx* c, int j, int m, const double* nrm2, z64* H, z64* gs, double* out_est) {
+  ++c->nlaunch;
   k_givens<<<1, 1, 0, c->st>>>(j, m, nrm2, H, gs, out_est);
   return cudaGetLastError();
 }
@@ -209,6 +215,7 @@ __global__ void k_scale_dev(const z64* x, const z64* sp, z64* dst, long long n) 
 }
 
 cudaError_t launch_scale(ddm_ctx* c, const z64* x, const z64* s, z64* dst, long long n) {
+  ++c->nlaunch;
   k_scale_dev<<<1216, 256, 0, c->st>>>(x, s, dst, n);
   return cudaGetLastError();
 }
@@ -219,6 +226,7 @@ __global__ void k_copy_scaled(const z64* src, double s, z64* dst, long long n) {
 }
 
 cudaError_t launch_copy_scaled(ddm_ctx* c, const z64* src, double s, z64* dst, long long n) {
+  ++c->nlaunch;
   k_copy_scaled<<<1216, 256, 0, c->st>>>(src, s, dst, n);
   return cudaGetLastError();
 }
@@ -230,6 +238,7 @@ __global__ void k_axpy(double s, const z64* w, z64* x, long long n) {
 }
 
 cudaError_t launch_axpy(ddm_ctx* c, double s, const z64* w, z64* x, long long n) {
+  ++c->nlaunch;
   k_axpy<<<1216, 256, 0, c->st>>>(s, w, x, n);
   return cudaGetLastError();
 }
@@ -258,7 +267,9 @@ __global__ void k_update_x(int j, int m, const z64* gs, const z64* Z, z64* x, lo
 }
 
 cudaError_t launch_lsq_update(ddm_ctx* c, int j, int m, z64* H, z64* gs, const z64* Z, z64* x, long long n) {
+  ++c->nlaunch;
   k_lsq<<<1, 1, 0, c->st>>>(j, m, H, gs);
+  ++c->nlaunch;
   k_update_x<<<RED_BLOCKS * 2, 256, 0, c->st>>>(j, m, gs, Z, x, n);
   return cudaGetLastError();
 }

@@ -31,6 +31,7 @@ __global__ void k_build_tables(z64* tab, const int* tdesc, int e, int ov, int np
 }
 
 cudaError_t launch_build_tables(ddm_ctx* c, const int* d_tdesc, int ntab, double sigma0, double power, int npml) {
+  ++c->nlaunch;
   k_build_tables<<<ntab, 128, 0, c->st>>>(c->d_tab, d_tdesc, c->e, c->p.overlap, npml, sigma0, power);
   return cudaGetLastError();
 }
@@ -44,6 +45,7 @@ __global__ void k_k2(double* k2, const double* cv, double omega, long long n) {
 }
 
 cudaError_t launch_k2(ddm_ctx* c, const double* c_dev) {
+  ++c->nlaunch;
   k_k2<<<608, 256, 0, c->st>>>(c->d_k2, c_dev, c->omega, c->g.nglob);
   return cudaGetLastError();
 }
@@ -85,6 +87,7 @@ __global__ void k_sub_hash(Geom g, unsigned long long* out) {
 }
 
 cudaError_t launch_sub_hash(ddm_ctx* c, unsigned long long* d_hash) {
+  ++c->nlaunch;
   k_sub_hash<<<c->g.nsub, 256, 0, c->st>>>(c->g, d_hash);
   return cudaGetLastError();
 }
@@ -105,7 +108,44 @@ __global__ void k_sub_compare(Geom g, const int* pairs, int* mismatch) {
 
 cudaError_t launch_sub_compare(ddm_ctx* c, const int* d_pairs, int npairs, int* d_mismatch) {
   if (npairs == 0) return cudaSuccess;
+  ++c->nlaunch;
   k_sub_compare<<<npairs, 256, 0, c->st>>>(c->g, d_pairs, d_mismatch);
+  return cudaGetLastError();
+}
+
+// Operator coefficients (assembly): per subdomain, planes of its local grid in the local
+// precision T -- plane 0 the centre, plane 1+2a the coupling to x - e_a, 2+2a to x + e_a --
+// evaluated in FP64 from the alpha tables and k^2 and rounded once; and the same planes of
+// the global operator in FP64.  blockIdx.y = subdomain (or nsub for the global box).
+template <typename T>
+__global__ void k_coefs(Geom g, cplx<T>* lc, z64* gc) {
+  const int nc = 2 * g.dim + 1;
+  if ((int)blockIdx.y < g.nsub) {
+    const SubDesc& s = g.subs[blockIdx.y];
+    long long len = (long long)s.ext[0] * s.ext[1] * s.ext[2];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+      int x[3] = {(int)(i % s.ext[0]), (int)((i / s.ext[0]) % s.ext[1]), (int)(i / ((long long)s.ext[0] * s.ext[1]))};
+      Coef cf = coef_at(g, s.tab, s.ext, x, g.k2[gindex(g, s, x)]);
+      cplx<T>* base = lc + s.vofs * nc + i;
+      base[0] = ccast<T>(cf.c);
+      for (int a = 0; a < g.dim; ++a) { base[(1 + 2 * a) * len] = ccast<T>(cf.m[a]); base[(2 + 2 * a) * len] = ccast<T>(cf.p[a]); }
+    }
+  } else {
+    long long n = g.nglob;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      int x[3] = {(int)(i % g.N[0]), (int)((i / g.N[0]) % g.N[1]), (int)(i / ((long long)g.N[0] * g.N[1]))};
+      Coef cf = coef_at(g, g.gtab, g.N, x, g.k2[i]);
+      gc[i] = cf.c;
+      for (int a = 0; a < g.dim; ++a) { gc[(1 + 2 * a) * n + i] = cf.m[a]; gc[(2 + 2 * a) * n + i] = cf.p[a]; }
+    }
+  }
+}
+
+cudaError_t launch_coefs(ddm_ctx* c) {
+  dim3 grid(64, c->g.nsub + 1);
+  ++c->nlaunch;
+  if (c->prec == DDM_MIXED) k_coefs<float><<<grid, 256, 0, c->st>>>(c->g, (c32*)c->d_lcoef, c->d_gcoef);
+  else k_coefs<double><<<grid, 256, 0, c->st>>>(c->g, (z64*)c->d_lcoef, c->d_gcoef);
   return cudaGetLastError();
 }
 
@@ -122,6 +162,7 @@ __global__ void k_rhs(Geom g, const z64* f, z64* b, int nrhs) {
 }
 
 cudaError_t launch_rhs(ddm_ctx* c, const z64* f, z64* b, int nrhs) {
+  ++c->nlaunch;
   k_rhs<<<1216, 256, 0, c->st>>>(c->g, f, b, nrhs);
   return cudaGetLastError();
 }
@@ -141,6 +182,7 @@ __global__ void k_beta(double* beta, int ov) {
 }
 
 cudaError_t launch_beta(ddm_ctx* c) {
+  ++c->nlaunch;
   k_beta<<<1, ((c->p.overlap + 32) / 32) * 32, 0, c->st>>>(c->d_beta, c->p.overlap);
   return cudaGetLastError();
 }

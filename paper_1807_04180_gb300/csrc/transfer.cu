@@ -54,6 +54,7 @@ static cudaError_t restrict_t(ddm_ctx* c, const z64* b, void* src, void* U, int 
   int maxlen = 0;
   for (auto& s : c->subs) maxlen = max(maxlen, s.ext[0] * s.ext[1] * s.ext[2]);
   dim3 grid((maxlen + 255) / 256, c->g.nsub, nrhs);
+  ++c->nlaunch;
   k_restrict<T><<<grid, 256, 0, c->st>>>(c->g, b, (cplx<T>*)src, (cplx<T>*)U);
   return cudaGetLastError();
 }
@@ -79,34 +80,37 @@ template <typename T>
 __device__ __forceinline__ cplx<T> beta_u(const Geom& g, const SubDesc& S, const int* d, const int* y,
                                           const cplx<T>* u) {
   // beta_d(y) u_S(y) at S-local node y (zero outside S's grid)
-  double b = 1.0;
+  T b = (T)1;
   for (int a = 0; a < g.dim; ++a) {
     if (y[a] < 0 || y[a] >= S.ext[a]) return mk<T>(0, 0);
     if (d[a] > 0) {            // sender's high-side cut-off beta_{->}: q = y - (e + nown)
       int q = y[a] - (g.e + S.nown[a]);
-      b *= (q < 0) ? 1.0 : (q >= g.ov ? 0.0 : g.beta[q]);
+      b *= (q < 0) ? (T)1 : (q >= g.ov ? (T)0 : (T)g.beta[q]);
     } else if (d[a] < 0) {     // sender's low-side cut-off beta_{<-}: q = (e - 1) - y
       int q = (g.e - 1) - y[a];
-      b *= (q < 0) ? 1.0 : (q >= g.ov ? 0.0 : g.beta[q]);
+      b *= (q < 0) ? (T)1 : (q >= g.ov ? (T)0 : (T)g.beta[q]);
     }
   }
-  if (b == 0.0) return mk<T>(0, 0);
+  if (b == (T)0) return mk<T>(0, 0);
   cplx<T> v = u[flat(y, S.ext)];
-  return mk<T>((T)b * v.x, (T)b * v.y);
+  return mk<T>(b * v.x, b * v.y);
 }
 
 template <typename T>
+struct CoefT { cplx<T> c, m[3], p[3]; };
+
+template <typename T>
 __device__ __forceinline__ cplx<T> psi_at(const Geom& g, const SubDesc& R, const SubDesc& S, const int* d,
-                                          const int* x, const Coef& cf, const cplx<T>* uS) {
+                                          const int* x, const CoefT<T>& cf, const cplx<T>* uS) {
   // -(A_R (beta_d u_S))(x): 5/7-point stencil of R at x applied to beta_d u_S
   int shift[3];
   for (int a = 0; a < 3; ++a) shift[a] = R.lo[a] - S.lo[a];   // R-local -> S-local
   int y[3] = {x[0] + shift[0], x[1] + shift[1], x[2] + shift[2]};
   cplx<T> acc = mk<T>(0, 0);
-  cfma(acc, ccast<T>(cf.c), beta_u<T>(g, S, d, y, uS));
+  cfma(acc, cf.c, beta_u<T>(g, S, d, y, uS));
   for (int a = 0; a < g.dim; ++a) {
-    if (x[a] + 1 < R.ext[a]) { y[a] += 1; cfma(acc, ccast<T>(cf.p[a]), beta_u<T>(g, S, d, y, uS)); y[a] -= 1; }
-    if (x[a] > 0) { y[a] -= 1; cfma(acc, ccast<T>(cf.m[a]), beta_u<T>(g, S, d, y, uS)); y[a] += 1; }
+    if (x[a] + 1 < R.ext[a]) { y[a] += 1; cfma(acc, cf.p[a], beta_u<T>(g, S, d, y, uS)); y[a] -= 1; }
+    if (x[a] > 0) { y[a] -= 1; cfma(acc, cf.m[a], beta_u<T>(g, S, d, y, uS)); y[a] += 1; }
   }
   return -acc;
 }
@@ -132,9 +136,13 @@ __global__ void k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* par
     cplx<T> acc_src = mk<T>(0, 0);
     cplx<T> acc_res = mk<T>(0, 0);
     if (near) {
-      int xg[3] = {R.lo[0] + x[0], R.lo[1] + x[1], R.lo[2] + x[2]};
-      double k2v = g.k2[((long long)xg[2] * g.N[1] + xg[1]) * g.N[0] + xg[0]];
-      Coef cf = coef_at(g, R.tab, R.ext, x, k2v);
+      CoefT<T> cf;
+      {
+        const int nc = 2 * g.dim + 1;
+        const cplx<T>* lc = (const cplx<T>*)g.lcoef + R.vofs * nc + i;
+        cf.c = lc[0];
+        for (int a = 0; a < g.dim; ++a) { cf.m[a] = lc[(1 + 2 * a) * len]; cf.p[a] = lc[(2 + 2 * a) * len]; }
+      }
       for (int code = 0; code < NDIR; ++code) {
         if (code == 13) continue;
         int d[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
@@ -195,6 +203,7 @@ static cudaError_t transfer_t(ddm_ctx* c, int s, void* src_next, double* part, i
   for (auto& sd : c->subs) maxlen = max(maxlen, sd.ext[0] * sd.ext[1] * sd.ext[2]);
   dim3 grid((maxlen + 255) / 256, c->g.nsub, nrhs);
   if (nblk) *nblk = grid.x;
+  ++c->nlaunch;
   k_transfer<T><<<grid, 256, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res);
   return cudaGetLastError();
 }
@@ -264,6 +273,7 @@ __global__ void k_assemble(Geom g, const cplx<T>* U, z64* w, int nrhs) {
 }
 
 cudaError_t launch_assemble(ddm_ctx* c, const void* U, z64* w, int nrhs) {
+  ++c->nlaunch;
   if (c->prec == DDM_MIXED)
     k_assemble<float><<<1216, 256, 0, c->st>>>(c->g, (const c32*)U, w, nrhs);
   else

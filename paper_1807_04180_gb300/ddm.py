@@ -69,6 +69,9 @@ def lib() -> ctypes.CDLL:
     sig = {
         "ddm_setup": [ctypes.POINTER(ddm_params), ctypes.c_double, _P, _P, ctypes.POINTER(_P)],
         "ddm_factor": [_P],
+        "ddm_set_medium": [_P, ctypes.c_double, _P],
+        "ddm_set_medium_host": [_P, ctypes.c_double, _P],
+        "ddm_kernel_launches": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
         "ddm_apply": [_P, ctypes.c_int, _P, _P, ctypes.c_int],
         "ddm_solve": [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                       ctypes.c_int, ctypes.POINTER(ddm_info)],
@@ -163,6 +166,22 @@ def ddm_setup(params: ddm_params, omega: float, c_dev, stream=None):
     st = lib().ddm_setup(ctypes.byref(params), float(omega), _ptr(c_dev), _stream(stream), ctypes.byref(out))
     _check(st, None)
     return out
+
+
+def ddm_set_medium(ctx, omega: float, c_dev) -> None:
+    _check(lib().ddm_set_medium(ctx, float(omega), _ptr(c_dev)), ctx)
+
+
+def ddm_set_medium_host(ctx, omega: float, c_host) -> None:
+    """c_host: float64 host array (numpy, or a pinned torch CPU tensor) on the global grid."""
+    ptr = c_host.data_ptr() if hasattr(c_host, "data_ptr") else np.ascontiguousarray(c_host, np.float64).ctypes.data
+    _check(lib().ddm_set_medium_host(ctx, float(omega), ptr), ctx)
+
+
+def ddm_kernel_launches(ctx, reset: bool = False) -> int:
+    n = ctypes.c_int64()
+    _check(lib().ddm_kernel_launches(ctx, ctypes.byref(n), int(bool(reset))), ctx)
+    return n.value
 
 
 def ddm_factor(ctx) -> None:

@@ -177,6 +177,40 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     }
   }
   g.ltotal = vofs;
+  // strip-node lists: every receiver node that some direction's chi_d covers, q in [0, ov]
+  // nodes inside each shared face (Section 2.2), with the directions as a bit mask
+  std::vector<int> sidx;
+  std::vector<unsigned> smask;
+  for (int sid = 0; sid < g.nsub; ++sid) {
+    SubDesc& s = c->subs[sid];
+    s.sofs = (int)sidx.size();
+    const long long len = (long long)s.ext[0] * s.ext[1] * s.ext[2];
+    for (long long li = 0; li < len; ++li) {
+      int x[3] = {(int)(li % s.ext[0]), (int)((li / s.ext[0]) % s.ext[1]), (int)(li / ((long long)s.ext[0] * s.ext[1]))};
+      unsigned mask = 0;
+      for (int code = 0; code < NDIR; ++code) {
+        if (code == 13 || s.nbr[code] < 0) continue;
+        int dd[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+        bool ok = true;
+        for (int a = 0; a < d; ++a) {
+          if (dd[a] > 0) { int q = x[a] - e; ok = ok && q >= 0 && q <= ov; }
+          else if (dd[a] < 0) { int q = e + s.nown[a] - 1 - x[a]; ok = ok && q >= 0 && q <= ov; }
+        }
+        if (ok) mask |= 1u << code;
+      }
+      if (!mask) continue;
+      bool own = true;
+      for (int a = 0; a < d; ++a) {
+        if (x[a] < e && !((s.at_lo >> a) & 1)) own = false;
+        if (x[a] >= e + s.nown[a] && !((s.at_hi >> a) & 1)) own = false;
+      }
+      sidx.push_back((int)li);
+      smask.push_back(mask | (own ? 0x80000000u : 0u));
+    }
+    s.scnt = (int)sidx.size() - s.sofs;
+    c->max_scnt = std::max(c->max_scnt, s.scnt);
+  }
+  if (sidx.empty()) { sidx.push_back(0); smask.push_back(0); }
   // owner tables (global extended index -> part along the axis)
   std::vector<int> owner;
   int own_ofs[3] = {0, 0, 0};
@@ -211,6 +245,8 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     ALLOC(c->d_tab, sizeof(z64) * tab_total);
     ALLOC(c->d_beta, sizeof(double) * (ov + 1));
     ALLOC(c->d_owner, sizeof(int) * owner.size());
+    ALLOC(c->d_sidx, sizeof(int) * sidx.size());
+    ALLOC(c->d_smask, sizeof(unsigned) * smask.size());
     ALLOC(c->d_cuts, sizeof(int) * cutsv.size());
     ALLOC(c->d_subs, sizeof(SubDesc) * g.nsub);
     ALLOC(c->d_err, sizeof(int));
@@ -227,10 +263,13 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
     CK(cudaMemcpyAsync(d_tdesc, tdesc.data(), sizeof(int) * tdesc.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_owner, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_sidx, sidx.data(), sizeof(int) * sidx.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->d_smask, smask.data(), sizeof(unsigned) * smask.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_cuts, cutsv.data(), sizeof(int) * cutsv.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDesc) * g.nsub, cudaMemcpyHostToDevice, c->st));
     g.k2 = c->d_k2; g.tab = c->d_tab; g.beta = c->d_beta; g.subs = c->d_subs;
     g.lcoef = c->d_lcoef; g.gcoef = c->d_gcoef;
+    g.sidx = c->d_sidx; g.smask = c->d_smask;
     for (int a = 0; a < 3; ++a) { g.owner[a] = c->d_owner + own_ofs[a]; g.cuts[a] = c->d_cuts + cut_ofs[a]; }
     CK(launch_build_tables(c, d_tdesc, (int)(tdesc.size() / 3), p->sigma0, p->pml_power, p->pml));
     CK(launch_k2(c, c_dev));
@@ -253,7 +292,7 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
 extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (!c) return DDM_OK;
   if (c->st || true) cudaStreamSynchronize(c->st);
-  void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
+  void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_sidx, c->d_smask, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
                   c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_V, c->d_Z, c->d_H, c->d_gs};
   for (void* q : ptrs) if (q) cudaFree(q);
@@ -402,6 +441,8 @@ static ddm_status run_steps(ddm_ctx* c, const z64* b, int nrhs, int K, z64* w_ou
       int nblk = 0;
       {
         TScope ts(c, T_TRANSFER);
+        // after step 1 the next source lives on the strip nodes only: clear the step-1 source once
+        if (s == 1) CK(cudaMemsetAsync(c->d_src, 0, local_elem(c) * c->g.ltotal * nrhs, c->st));
         CK(launch_transfer_n(c, s, c->d_src, c->d_part, nrhs, want_res ? 1 : 0, &nblk));
       }
       if (want_res) {

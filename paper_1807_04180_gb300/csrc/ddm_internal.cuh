@@ -62,7 +62,9 @@ struct SubDesc {
   int fid;             // factor id
   int at_lo;           // bit a set: low side of axis a is on the global boundary
   int at_hi;           // bit a set: high side of axis a is on the global boundary
-  int pad;
+  int pad;            // leading dimension of its factor blocks
+  int sofs, scnt;      // its range in the strip-node list (nodes that receive a transfer)
+  int pad2;
   long long vofs;      // offset of its local vector
   long long fofs;      // element offset of its factor (blocks of b x ldb)
   int nbr[NDIR];       // neighbour id per direction code, -1 if none (nbr[13] = self)
@@ -82,6 +84,8 @@ struct Geom {
   const SubDesc* subs;
   const void* lcoef;      // per-subdomain operator planes (local precision)
   const z64* gcoef;       // global operator planes (FP64)
+  const int* sidx;           // strip-node list: local node index
+  const unsigned* smask;     // strip-node list: bit d = receives direction code d; bit 31 = own region
   const int* owner[MAXDIM];  // part owning global extended index g along axis a
   const int* cuts[MAXDIM];   // parts+1 cuts per axis
   int parts[MAXDIM];
@@ -148,6 +152,9 @@ struct ddm_ctx {
   ddm::z64* d_tab = nullptr;
   double* d_beta = nullptr;
   int* d_owner = nullptr;
+  int* d_sidx = nullptr;
+  unsigned* d_smask = nullptr;
+  int max_scnt = 0;
   int* d_cuts = nullptr;
   int* d_err = nullptr;
   double* d_part = nullptr;      // reduction partials

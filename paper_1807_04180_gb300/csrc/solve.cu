@@ -22,7 +22,10 @@ namespace ddm {
 constexpr int SOLVE_NCW = 8;     // consumer warps
 constexpr int SOLVE_RCH = 16;    // columns of G_k per pipeline chunk
 constexpr int SOLVE_THREADS = (SOLVE_NCW + 1) * 32;
-constexpr long long WAIT_LIMIT = 1LL << 22;
+// bounded waits: each try_wait may suspend the thread up to WAIT_HINT_NS until the phase
+// completes; WAIT_LIMIT tries (about 4 s at most) before giving up
+constexpr long long WAIT_LIMIT = 1LL << 18;
+constexpr uint32_t WAIT_HINT_NS = 16384;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -38,9 +41,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(a), "r"(parity)
+      : "r"(a), "r"(parity), "r"(WAIT_HINT_NS)
       : "memory");
   return ok != 0;
 }
@@ -64,10 +67,10 @@ __device__ __forceinline__ void seq_block(int i, int m, int& pass, int& k) {
   k = pass == 0 ? i : 2 * m - 2 - i;
 }
 
-template <typename T, int NR, int NST>
+template <typename T, int NR>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_solve2d(Geom g, const cplx<T>* __restrict__ G,
                                                           const cplx<T>* __restrict__ src, cplx<T>* out,
-                                                          cplx<T>* U, int nrhs, int* err) {
+                                                          cplx<T>* U, int nrhs, int nst, int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
   const SubDesc& s = g.subs[blockIdx.x];
   const int b = s.ext[0], m = s.ext[1], ldb = s.pad;
@@ -77,18 +80,15 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve2d(Geom g, const cplx<T>
   const int nch = (b + SOLVE_RCH - 1) / SOLVE_RCH;
   const int nblk = 2 * m - 1;
 
-  cplx<T>* stage = (cplx<T>*)smem;                                   // NST x RCH x ldb
-  cplx<T>* ys = stage + (size_t)NST * SOLVE_RCH * ldb;               // NR x bpad: right-hand side of the block GEMV
-  cplx<T>* ts = ys + NR * bpad;                                      // NR x bpad: outputs of the previous block
-  cplx<T>* tk = ts + NR * bpad;                                      // NR x bpad: t_k (backward)
-  cplx<T>* uk = tk + NR * bpad;                                      // NR x bpad: U_k before accumulation
-  cplx<T>* red = uk + NR * bpad;                                     // NR x bpad: second-half partial sums
+  cplx<T>* stage = (cplx<T>*)smem;                                   // nst x RCH x ldb
+  cplx<T>* ys = stage + (size_t)nst * SOLVE_RCH * ldb;               // NR x bpad: right-hand side of the block GEMV
+  cplx<T>* red = ys + NR * bpad;                                     // NR x bpad: second-half partial sums
   uint64_t* bars = (uint64_t*)(((uintptr_t)(red + NR * bpad) + 15) & ~(uintptr_t)15);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NST);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + nst);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int i = 0; i < NST; ++i) { mbar_init(full0 + 8 * i, 1); mbar_init(empty0 + 8 * i, SOLVE_NCW); }
+    for (int i = 0; i < nst; ++i) { mbar_init(full0 + 8 * i, 1); mbar_init(empty0 + 8 * i, SOLVE_NCW); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -96,28 +96,35 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve2d(Geom g, const cplx<T>
   if (warp == SOLVE_NCW) {
     // ---------------- producer: column chunks of G_k in consumption order ----------------
     if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;            // phase of the current pass over the ring
       long long c = 0;
       for (int i = 0; i < nblk; ++i) {
         int pass, k;
         seq_block(i, m, pass, k);
         for (int ch = 0; ch < nch; ++ch, ++c) {
-          const int st = (int)(c % NST);
-          if (c >= NST) mbar_wait(empty0 + 8 * st, (uint32_t)((c / NST - 1) & 1), err);
+          if (c >= nst) mbar_wait(empty0 + 8 * st, ph ^ 1u, err);
           const int cols = min(SOLVE_RCH, b - ch * SOLVE_RCH);
           const uint32_t bytes = (uint32_t)(cols * ldb * (int)sizeof(cplx<T>));
           mbar_expect_tx(full0 + 8 * st, bytes);
           bulk_g2s(smem_u32(stage + (size_t)st * SOLVE_RCH * ldb),
                    G + s.fofs + ((long long)k * b + ch * SOLVE_RCH) * ldb, bytes, full0 + 8 * st);
+          if (++st == nst) { st = 0; ph ^= 1u; }
         }
       }
+      // bounded wait for the copies still in flight before the CTA may exit
       const long long total = (long long)nblk * nch;
-      for (long long cc = max(0LL, total - NST); cc < total; ++cc)   // bounded wait for copies in flight
-        mbar_wait(full0 + 8 * (int)(cc % NST), (uint32_t)((cc / NST) & 1), err);
+      for (long long cc = max(0LL, total - nst); cc < total; ++cc)
+        mbar_wait(full0 + 8 * (int)(cc % nst), (uint32_t)((cc / nst) & 1), err);
     }
     return;
   }
 
   // ---------------- consumers ----------------
+  // thread (half, row): half 0 owns row `row` of every block vector (epilogue, next right-hand
+  // side, prefetch); both halves accumulate the GEMV over their half of each chunk.
+  const int row = tid & 127, half = tid >> 7;
+  const bool owner = half == 0 && row < b;
   const long long lt = g.ltotal;
   const long long len = (long long)b * m;
   const cplx<T>* srcv = src + (long long)r0 * lt + s.vofs;
@@ -126,137 +133,141 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve2d(Geom g, const cplx<T>
   const cplx<T>* lc = (const cplx<T>*)g.lcoef + s.vofs * 5;      // planes: C, W, E, S, N
   const cplx<T>* cSp = lc + 3 * len;
   const cplx<T>* cNp = lc + 4 * len;
-  constexpr int PI = (NR * 128 + SOLVE_NCW * 32 - 1) / (SOLVE_NCW * 32);   // items per thread (b <= 128)
-  const int nitem = nr * b;
-  // prefetched per-block values: forward (src_k, c_S(k)) or backward (t_k, U_k, c_N(k))
-  cplx<T> pa[PI], pb[PI], pc[PI];
+  // per-row registers: prefetched values of the next block (pa: src_k or t_k, pb: U_k,
+  // pc: c_S(k) or c_N(k)), the current block's t_k (tk) and U_k (uk), and the last output t
+  cplx<T> pa[NR], pb[NR], tk[NR], uk[NR], tv[NR];
+  cplx<T> pc = mk<T>(0, 0);
   auto load_block = [&](int i) {
     int pass, k;
     seq_block(i, m, pass, k);
+    const long long o = (long long)k * b + row;
+    pc = pass == 0 ? (k > 0 ? cSp[o] : mk<T>(0, 0)) : cNp[o];
 #pragma unroll
-    for (int q = 0; q < PI; ++q) {
-      const int idx = tid + q * SOLVE_NCW * 32;
-      if (idx < nitem) {
-        const int rr = idx / b, j = idx - rr * b;
-        const long long o = (long long)rr * lt + (long long)k * b + j;
-        if (pass == 0) {
-          pa[q] = srcv[o];
-          pc[q] = k > 0 ? cSp[(long long)k * b + j] : mk<T>(0, 0);
-          pb[q] = (Uv && k == m - 1) ? Uv[o] : mk<T>(0, 0);
-        } else {
-          pa[q] = outv[o];
-          pc[q] = cNp[(long long)k * b + j];
-          pb[q] = Uv ? Uv[o] : mk<T>(0, 0);
-        }
+    for (int rr = 0; rr < NR; ++rr) {
+      if (rr < nr) {
+        const long long oo = (long long)rr * lt + o;
+        pa[rr] = pass == 0 ? srcv[oo] : outv[oo];
+        pb[rr] = (Uv && (pass == 1 || k == m - 1)) ? Uv[oo] : mk<T>(0, 0);
       }
     }
   };
-  load_block(0);
-  long long c = 0;
+  // right-hand side of block i from the prefetched values and the previous output tv:
+  // forward y_k = r_k - c_S(., k) t_{k-1}; backward z = c_N(., k) x_{k+1}
+  auto form_rhs = [&](int i) {
+    int pass, k;
+    seq_block(i, m, pass, k);
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) {
+      if (rr < nr) {
+        cplx<T> y;
+        if (pass == 0) {
+          y = pa[rr];
+          if (k > 0) y = y - pc * tv[rr];
+        } else {
+          y = pc * tv[rr];
+          tk[rr] = pa[rr];
+        }
+        uk[rr] = pb[rr];
+        ys[rr * bpad + row] = y;
+      }
+    }
+  };
+  if (owner) {
+    load_block(0);
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) tv[rr] = mk<T>(0, 0);
+    form_rhs(0);
+    if (nblk > 1) load_block(1);
+  }
+  consumer_sync();
+  int st = 0;
+  uint32_t ph = 0;
   for (int i = 0; i < nblk; ++i) {
     int pass, k;
     seq_block(i, m, pass, k);
-    // flush the previous block's outputs (coalesced), stage this block's vectors, form y
-#pragma unroll
-    for (int q = 0; q < PI; ++q) {
-      const int idx = tid + q * SOLVE_NCW * 32;
-      if (idx < nitem) {
-        const int rr = idx / b, j = idx - rr * b;
-        const int sidx = rr * bpad + j;
-        if (i > 0) {
-          int pp, pk;
-          seq_block(i - 1, m, pp, pk);
-          const long long o = (long long)rr * lt + (long long)pk * b + j;
-          const cplx<T> v = ts[sidx];
-          outv[o] = v;
-          if (Uv && (pp == 1 || pk == m - 1)) Uv[o] = uk[sidx] + v;
-        }
-        cplx<T> y;
-        if (pass == 0) {
-          y = pa[q];
-          if (k > 0) y = y - pc[q] * ts[sidx];      // y_k = r_k - c_S(., k) t_{k-1}
-        } else {
-          y = pc[q] * ts[sidx];                      // z = c_N(., k) x_{k+1}
-          tk[sidx] = pa[q];
-        }
-        ys[sidx] = y;
-        uk[sidx] = pb[q];
-      }
-    }
-    if (i + 1 < nblk) load_block(i + 1);
-    consumer_sync();
-    // G_k y: thread (half h, row i) accumulates its row over the columns of each chunk that
-    // fall in its half; the halves are combined at the end of the block
     cplx<T> acc[NR];
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) acc[rr] = mk<T>(0, 0);
-    const int row = tid & 127, half = tid >> 7;
-    for (int ch = 0; ch < nch; ++ch, ++c) {
-      const int st = (int)(c % NST);
-      mbar_wait(full0 + 8 * st, (uint32_t)((c / NST) & 1), err);
+    for (int ch = 0; ch < nch; ++ch) {
+      mbar_wait(full0 + 8 * st, ph, err);
       const cplx<T>* sg = stage + (size_t)st * SOLVE_RCH * ldb;   // columns ch*16 .. ch*16+15
       if (row < b) {
         const int j0 = ch * SOLVE_RCH + half * (SOLVE_RCH / 2);
         const int jn = min(SOLVE_RCH / 2, b - j0);
-#pragma unroll 8
-        for (int jj = 0; jj < SOLVE_RCH / 2; ++jj) {
-          if (jj >= jn) break;
-          const cplx<T> gv = sg[(half * (SOLVE_RCH / 2) + jj) * ldb + row];
+        const cplx<T>* gcol = sg + (half * (SOLVE_RCH / 2)) * ldb + row;
+        if (jn == SOLVE_RCH / 2) {     // full half-chunk: straight-line, loads hoisted
+          cplx<T> gv[SOLVE_RCH / 2];
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr)
-            if (rr < nr) cfma(acc[rr], gv, ys[rr * bpad + j0 + jj]);
+          for (int jj = 0; jj < SOLVE_RCH / 2; ++jj) gv[jj] = gcol[jj * ldb];
+#pragma unroll
+          for (int jj = 0; jj < SOLVE_RCH / 2; ++jj)
+#pragma unroll
+            for (int rr = 0; rr < NR; ++rr)
+              if (rr < nr) cfma(acc[rr], gv[jj], ys[rr * bpad + j0 + jj]);
+        } else {
+          for (int jj = 0; jj < jn; ++jj) {
+            const cplx<T> gv = gcol[jj * ldb];
+#pragma unroll
+            for (int rr = 0; rr < NR; ++rr)
+              if (rr < nr) cfma(acc[rr], gv, ys[rr * bpad + j0 + jj]);
+          }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8 * st);
+      if (++st == nst) { st = 0; ph ^= 1u; }
     }
     if (half == 1 && row < b) {
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr) if (rr < nr) red[rr * bpad + row] = acc[rr];
     }
     consumer_sync();
-    if (half == 0 && row < b) {
+    if (owner) {
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr) {
         if (rr < nr) {
-          const int sidx = rr * bpad + row;
-          const cplx<T> v = acc[rr] + red[sidx];
-          ts[sidx] = pass == 0 ? v : tk[sidx] - v;     // t_k, or x_k = t_k - G_k z
+          const cplx<T> v = acc[rr] + red[rr * bpad + row];
+          tv[rr] = pass == 0 ? v : tk[rr] - v;                     // t_k, or x_k = t_k - G_k z
+          const long long o = (long long)rr * lt + (long long)k * b + row;
+          outv[o] = tv[rr];
+          if (Uv && (pass == 1 || k == m - 1)) Uv[o] = uk[rr] + tv[rr];
         }
+      }
+      if (i + 1 < nblk) {
+        form_rhs(i + 1);
+        if (i + 2 < nblk) load_block(i + 2);
       }
     }
     consumer_sync();
-  }
-  // flush the last block (backward k = 0)
-#pragma unroll
-  for (int q = 0; q < PI; ++q) {
-    const int idx = tid + q * SOLVE_NCW * 32;
-    if (idx < nitem) {
-      const int rr = idx / b, j = idx - rr * b;
-      const int sidx = rr * bpad + j;
-      int pp, pk;
-      seq_block(nblk - 1, m, pp, pk);
-      const long long o = (long long)rr * lt + (long long)pk * b + j;
-      outv[o] = ts[sidx];
-      if (Uv) Uv[o] = uk[sidx] + ts[sidx];
-    }
   }
 }
 
 template <typename T, int NR>
 static cudaError_t solve_nr(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
-  constexpr int NST = sizeof(T) == 4 ? 6 : 4;
-  int maxb = 0, maxm = 0, maxld = 0;
-  for (auto& s : c->subs) { maxb = std::max(maxb, s.ext[0]); maxm = std::max(maxm, s.ext[1]); maxld = std::max(maxld, s.pad); }
+  int maxb = 0, maxld = 0;
+  for (auto& s : c->subs) { maxb = std::max(maxb, s.ext[0]); maxld = std::max(maxld, s.pad); }
   const int bpad = (maxb + 3) & ~3;
-  size_t el = sizeof(cplx<T>);
-  size_t sm = (size_t)NST * SOLVE_RCH * maxld * el + (size_t)5 * NR * bpad * el + 16 + 2 * NST * 8 + 16;
-  cudaError_t e = cudaFuncSetAttribute(k_solve2d<T, NR, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t el = sizeof(cplx<T>);
+  const size_t fixed = (size_t)2 * NR * bpad * el + 16 + 2 * 32 * 8 + 16;
+  const size_t stage = (size_t)SOLVE_RCH * maxld * el;
+  // as many pipeline stages as fit while every CTA of the grid is resident at once
+  int dev = 0, nsm = 152, smem_sm = 228 * 1024, smem_blk = 227 * 1024;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const long long ctas = (long long)c->g.nsub * ((nrhs + NR - 1) / NR);
+  const int per_sm = (int)std::min<long long>(4, std::max<long long>(1, (ctas + nsm - 1) / nsm));
+  size_t budget = std::min<size_t>((size_t)smem_blk, (size_t)smem_sm / per_sm - 1024);
+  int nst = (int)std::min<size_t>(32, budget > fixed ? (budget - fixed) / stage : 0);
+  nst = std::max(nst, 2);
+  const size_t sm = fixed + (size_t)nst * stage;
+  cudaError_t e = cudaFuncSetAttribute(k_solve2d<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid(c->g.nsub, (nrhs + NR - 1) / NR);
   ++c->nlaunch;
-  k_solve2d<T, NR, NST><<<grid, SOLVE_THREADS, sm, c->st>>>(c->g, (const cplx<T>*)c->d_G, (const cplx<T>*)src,
-                                                           (cplx<T>*)out, (cplx<T>*)U, nrhs, c->d_err);
+  k_solve2d<T, NR><<<grid, SOLVE_THREADS, sm, c->st>>>(c->g, (const cplx<T>*)c->d_G, (const cplx<T>*)src,
+                                                     (cplx<T>*)out, (cplx<T>*)U, nrhs, nst, c->d_err);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,8 @@
 // Source restriction, the fused directional-residual transfer (the Psi operators of
 // Section 2.2 in Eq. (talg_2)) with residual-norm partials, and the assembly of the DDM
 // solution (Eq. (tsum)).
+#include <algorithm>
+
 #include "ddm_internal.cuh"
 
 namespace ddm {
@@ -69,109 +71,107 @@ cudaError_t launch_restrict(ddm_ctx* c, const z64* b, void* src, void* U, int nr
 //   res(x)         = sum_d Psi_d(u^s + .. + u^{s-lag(d)+1})(x)  on R's own region,
 // with Psi_d(v) = -A_R(beta_d v) chi_d, beta_d the sender's cut-off(s) facing R and chi_d
 // the receiver's side of the shared face(s) (Section 2.2).  Psi_d is non-zero only on
-// receiver nodes at most ov nodes inside each shared face.  Sums of |res|^2 per block go to
-// part[(r * nsub + R) * gridDim.x + blockIdx.x].
+// receiver nodes at most ov nodes inside each shared face: the threads run over R's
+// strip-node list (built at set-up: local index plus the mask of directions that reach the
+// node), and beta_d is evaluated as a product of 1D cut-offs.  Sums of |res|^2 per block go
+// to part[(r * nsub + R) * gridDim.x + blockIdx.x].
 // ring[t % L] holds u^t (local layout), L = dim; res_slot[k] is the slot of u^{s-k}
 // (-1 when s-k < 1, i.e. u = 0).
 // ---------------------------------------------------------------------------
 struct RingPtrs { const void* p[3]; int res_slot[3]; };
 
 template <typename T>
-__device__ __forceinline__ cplx<T> beta_u(const Geom& g, const SubDesc& S, const int* d, const int* y,
-                                          const cplx<T>* u) {
-  // beta_d(y) u_S(y) at S-local node y (zero outside S's grid)
-  T b = (T)1;
-  for (int a = 0; a < g.dim; ++a) {
-    if (y[a] < 0 || y[a] >= S.ext[a]) return mk<T>(0, 0);
-    if (d[a] > 0) {            // sender's high-side cut-off beta_{->}: q = y - (e + nown)
-      int q = y[a] - (g.e + S.nown[a]);
-      b *= (q < 0) ? (T)1 : (q >= g.ov ? (T)0 : (T)g.beta[q]);
-    } else if (d[a] < 0) {     // sender's low-side cut-off beta_{<-}: q = (e - 1) - y
-      int q = (g.e - 1) - y[a];
-      b *= (q < 0) ? (T)1 : (q >= g.ov ? (T)0 : (T)g.beta[q]);
-    }
-  }
-  if (b == (T)0) return mk<T>(0, 0);
-  cplx<T> v = u[flat(y, S.ext)];
-  return mk<T>(b * v.x, b * v.y);
-}
-
-template <typename T>
 struct CoefT { cplx<T> c, m[3], p[3]; };
 
 template <typename T>
-__device__ __forceinline__ cplx<T> psi_at(const Geom& g, const SubDesc& R, const SubDesc& S, const int* d,
-                                          const int* x, const CoefT<T>& cf, const cplx<T>* uS) {
-  // -(A_R (beta_d u_S))(x): 5/7-point stencil of R at x applied to beta_d u_S
-  int shift[3];
-  for (int a = 0; a < 3; ++a) shift[a] = R.lo[a] - S.lo[a];   // R-local -> S-local
-  int y[3] = {x[0] + shift[0], x[1] + shift[1], x[2] + shift[2]};
-  cplx<T> acc = mk<T>(0, 0);
-  cfma(acc, cf.c, beta_u<T>(g, S, d, y, uS));
-  for (int a = 0; a < g.dim; ++a) {
-    if (x[a] + 1 < R.ext[a]) { y[a] += 1; cfma(acc, cf.p[a], beta_u<T>(g, S, d, y, uS)); y[a] -= 1; }
-    if (x[a] > 0) { y[a] -= 1; cfma(acc, cf.m[a], beta_u<T>(g, S, d, y, uS)); y[a] += 1; }
-  }
-  return -acc;
-}
-
-template <typename T>
-__global__ void k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res) {
+__global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res) {
   const int Rid = blockIdx.y;
   const SubDesc& R = g.subs[Rid];
   const int r = blockIdx.z;
-  long long len = (long long)R.ext[0] * R.ext[1] * R.ext[2];
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int e = g.e, ov = g.ov, dim = g.dim;
+  __shared__ T beta_s[32];
+  if (threadIdx.x <= ov && threadIdx.x < 32) beta_s[threadIdx.x] = (T)g.beta[threadIdx.x];
+  __syncthreads();
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
   double res2 = 0.0;
-  if (i < len) {
+  if (it < R.scnt) {
+    const int li = g.sidx[R.sofs + it];
+    const unsigned mask = g.smask[R.sofs + it];
     int x[3];
-    unflat(i, R.ext, x);
-    // depth of x inside each face: q_lo = x - e (for d = +1), q_hi = e + nown - 1 - x (d = -1)
-    bool near = false;
-    for (int a = 0; a < g.dim; ++a) {
-      int ql = x[a] - g.e, qh = g.e + R.nown[a] - 1 - x[a];
-      if ((ql >= 0 && ql <= g.ov && !((R.at_lo >> a) & 1)) || (qh >= 0 && qh <= g.ov && !((R.at_hi >> a) & 1)))
-        near = true;
+    unflat(li, R.ext, x);
+    const long long len = (long long)R.ext[0] * R.ext[1] * R.ext[2];
+    CoefT<T> cf;
+    {
+      const int nc = 2 * dim + 1;
+      const cplx<T>* lc = (const cplx<T>*)g.lcoef + R.vofs * nc + li;
+      cf.c = lc[0];
+      for (int a = 0; a < dim; ++a) { cf.m[a] = lc[(1 + 2 * a) * len]; cf.p[a] = lc[(2 + 2 * a) * len]; }
     }
-    cplx<T> acc_src = mk<T>(0, 0);
-    cplx<T> acc_res = mk<T>(0, 0);
-    if (near) {
-      CoefT<T> cf;
-      {
-        const int nc = 2 * g.dim + 1;
-        const cplx<T>* lc = (const cplx<T>*)g.lcoef + R.vofs * nc + i;
-        cf.c = lc[0];
-        for (int a = 0; a < g.dim; ++a) { cf.m[a] = lc[(1 + 2 * a) * len]; cf.p[a] = lc[(2 + 2 * a) * len]; }
-      }
-      for (int code = 0; code < NDIR; ++code) {
-        if (code == 13) continue;
-        int d[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
-        if (g.dim == 2 && d[2] != 0) continue;
-        int Sid = R.nbr[code];
-        if (Sid < 0) continue;
-        bool ok = true;
-        int lagd = 0;
-        for (int a = 0; a < g.dim; ++a) {
-          if (d[a] > 0) { int q = x[a] - g.e; ok = ok && q >= 0 && q <= g.ov; ++lagd; }
-          else if (d[a] < 0) { int q = g.e + R.nown[a] - 1 - x[a]; ok = ok && q >= 0 && q <= g.ov; ++lagd; }
-        }
-        if (!ok) continue;
-        const SubDesc& S = g.subs[Sid];
-        // p_k = Psi_d(u^{s-k}), k = 0..lag-1: the source for step s+1 takes k = lag-1
-        // (u^{s+1-lag}); the residual sums all of them.
-        for (int k = 0; k < lagd; ++k) {
-          if (!want_res && k != lagd - 1) continue;
-          int sl = ring.res_slot[k];
-          if (sl < 0) continue;
-          const cplx<T>* u = (const cplx<T>*)ring.p[sl] + (long long)r * g.ltotal + S.vofs;
-          cplx<T> pv = psi_at<T>(g, R, S, d, x, cf, u);
-          if (k == lagd - 1) acc_src = acc_src + pv;
-          acc_res = acc_res + pv;
+    cplx<T> acc_src = mk<T>(0, 0), acc_res = mk<T>(0, 0);
+    unsigned dm = mask & 0x07ffffffu;
+    while (dm) {
+      const int code = __ffs(dm) - 1;
+      dm &= dm - 1;
+      const int d[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+      const int lagd = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
+      const SubDesc& S = g.subs[R.nbr[code]];
+      // the stencil of x in S-local coordinates and the sender's cut-off there (1D factors)
+      int y0[3];
+      for (int a = 0; a < 3; ++a) y0[a] = x[a] + R.lo[a] - S.lo[a];
+      // per axis: cut-off at offsets -1, 0, +1 along that axis (beta_d is a product of 1D cut-offs)
+      T bw[3][3];
+      bool inside[3][3];
+      for (int a = 0; a < 3; ++a) {
+        for (int o = -1; o <= 1; ++o) {
+          const int ya = y0[a] + o;
+          T bb = (T)1;
+          bool in = a < dim ? (ya >= 0 && ya < S.ext[a]) : (o == 0);
+          if (a < dim && d[a] != 0) {
+            const int q = d[a] > 0 ? ya - (e + S.nown[a]) : (e - 1) - ya;
+            bb = q < 0 ? (T)1 : (q >= ov ? (T)0 : beta_s[q]);
+          }
+          bw[a][o + 1] = bb;
+          inside[a][o + 1] = in;
         }
       }
-      if (want_res && in_own(g, R, x)) res2 = (double)acc_res.x * acc_res.x + (double)acc_res.y * acc_res.y;
+      for (int k = 0; k < lagd; ++k) {
+        if (!want_res && k != lagd - 1) continue;
+        const int sl = ring.res_slot[k];
+        if (sl < 0) continue;
+        const cplx<T>* u = (const cplx<T>*)ring.p[sl] + (long long)r * g.ltotal + S.vofs;
+        // -(A_R (beta_d u_S))(x)
+        cplx<T> acc = mk<T>(0, 0);
+        {
+          const T w0 = bw[0][1] * bw[1][1] * bw[2][1];
+          if (w0 != (T)0 && inside[0][1] && inside[1][1] && inside[2][1]) {
+            const cplx<T> v = u[flat(y0, S.ext)];
+            cfma(acc, cf.c, mk<T>(w0 * v.x, w0 * v.y));
+          }
+        }
+        for (int a = 0; a < dim; ++a) {
+          for (int o = -1; o <= 1; o += 2) {
+            if ((o > 0 && x[a] + 1 >= R.ext[a]) || (o < 0 && x[a] == 0)) continue;   // R's Dirichlet ghost
+            if (!inside[a][o + 1]) continue;
+            bool okin = true;
+            T w = (T)1;
+            for (int bax = 0; bax < 3; ++bax) {
+              const int oo = bax == a ? o + 1 : 1;
+              okin = okin && inside[bax][oo];
+              w *= bw[bax][oo];
+            }
+            if (!okin || w == (T)0) continue;
+            int yy[3] = {y0[0], y0[1], y0[2]};
+            yy[a] += o;
+            const cplx<T> v = u[flat(yy, S.ext)];
+            cfma(acc, o > 0 ? cf.p[a] : cf.m[a], mk<T>(w * v.x, w * v.y));
+          }
+        }
+        if (k == lagd - 1) acc_src = acc_src - acc;
+        acc_res = acc_res - acc;
+      }
     }
-    src_next[(long long)r * g.ltotal + R.vofs + i] = acc_src;
+    src_next[(long long)r * g.ltotal + R.vofs + li] = acc_src;
+    if (want_res && (mask & 0x80000000u)) res2 = (double)acc_res.x * acc_res.x + (double)acc_res.y * acc_res.y;
   }
   if (want_res) {
     for (int o = 16; o; o >>= 1) res2 += __shfl_xor_sync(0xffffffffu, res2, o);
@@ -199,12 +199,10 @@ static cudaError_t transfer_t(ddm_ctx* c, int s, void* src_next, double* part, i
     int t = s - k;
     rp.res_slot[k] = (k < L && t >= 1) ? (t % L) : -1;
   }
-  int maxlen = 0;
-  for (auto& sd : c->subs) maxlen = max(maxlen, sd.ext[0] * sd.ext[1] * sd.ext[2]);
-  dim3 grid((maxlen + 255) / 256, c->g.nsub, nrhs);
+  dim3 grid((std::max(c->max_scnt, 1) + 127) / 128, c->g.nsub, nrhs);
   if (nblk) *nblk = grid.x;
   ++c->nlaunch;
-  k_transfer<T><<<grid, 256, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res);
+  k_transfer<T><<<grid, 128, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res);
   return cudaGetLastError();
 }
 

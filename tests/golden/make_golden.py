@@ -1,8 +1,9 @@
 """Write full-size golden records from the FP64 oracle only (no CUDA path involved).
 
-    python tests/golden/make_golden.py heterogeneous-1024
+    python tests/golden/make_golden.py heterogeneous-1024 [K]
 
-For the 2D heterogeneous workload (1024^2 interior, 16x16 subdomains, K = 2, restart 60) it
+For the 2D heterogeneous workload (1024^2 interior, 16x16 subdomains, K DDM steps per
+preconditioner application (default 2), restart 60) it
 runs the oracle's DDM-preconditioned FGMRES to a relative residual of 1e-10 and stores: the
 residual-estimate history (so the iteration count to 1e-6 is the first entry <= 1e-6), and the
 solution at 512 seeded interior nodes plus the 64 nodes around the source.  The GPU tests
@@ -36,8 +37,9 @@ def sample_indices(gshape, e, f, seed=7, count=512):
     return np.array(idx, dtype=np.int64)
 
 
-def heterogeneous_1024(workers):
+def heterogeneous_1024(workers, K):
     wl = W.heterogeneous_2d()
+    wl.K = K
     t0 = time.time()
     o = DDMOracle(wl.n, wl.h, wl.cuts, wl.ov, wl.npml, wl.sigma0, wl.power, wl.omega, wl.c, workers=workers)
     o.factor()
@@ -60,9 +62,10 @@ def heterogeneous_1024(workers):
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "heterogeneous-1024"
+    K = int(sys.argv[2]) if len(sys.argv) > 2 else 2
     workers = int(os.environ.get("ORACLE_WORKERS", os.cpu_count() or 1))
-    out = {"heterogeneous-1024": heterogeneous_1024}[which](workers)
-    path = os.path.join(HERE, f"oracle_{which}.json")
+    out = {"heterogeneous-1024": heterogeneous_1024}[which](workers, K)
+    path = os.path.join(HERE, f"oracle_{which}.json" if K == 2 else f"oracle_{which}_K{K}.json")
     with open(path, "w") as fh:
         json.dump(out, fh)
     print(path, out["fgmres_iters_to_1e-6"], out["fgmres_iters_to_1e-10"], out["explicit_rel_residual"],

@@ -214,6 +214,31 @@ ddm_status ddm_kernel_launches(ddm_ctx *ctx, int64_t *count, int reset);
  * per sweep, per subdomain using it), and bytes of factor storage.          */
 ddm_status ddm_factor_bytes(const ddm_ctx *ctx, int64_t *bytes_per_solve, int64_t *bytes_stored);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free helper.  The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory where they need it (a fixed
+ * device-memory budget, a caching allocator that must not be re-entered, or a
+ * section where cudaMalloc's implicit device synchronisation is not allowed).
+ * ------------------------------------------------------------------------ */
+
+/* norms_dev[i] = ||x_i||_2 for nvec complex128 vectors of n elements each,
+ * stored one after another at x_dev (device).  norms_dev is a caller-owned
+ * device array of nvec doubles.  Work is enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default) and the call returns without
+ * synchronising; read norms_dev after the stream has reached it.
+ *
+ * Allocates nothing: its reduction scratch is one static device array of
+ * 304 x 16 + 16 doubles (about 39 KB) that every GPU which loads the library
+ * keeps until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device current) and
+ * caches it; make that first call outside any stream capture.  All calls
+ * share the one array, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Errors: DDM_E_INVAL for null pointers, n < 1 or nvec outside [1, 16] (the
+ * static scratch holds 16 vectors), DDM_E_CUDA; the message is readable with
+ * ddm_last_error(NULL).                                                      */
+ddm_status ddm_norms_noalloc(const void *x_dev, int64_t n, int nvec, void *stream, double *norms_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,11 @@ using namespace ddm;
 
 static std::string g_setup_err;
 
+namespace ddm {
+// message of a failed call that has no context (read with ddm_last_error(NULL))
+void set_global_error(const std::string& msg) { g_setup_err = msg; }
+}  // namespace ddm
+
 static ddm_status fail(ddm_ctx* c, ddm_status st, const std::string& msg) {
   if (c) c->err = msg; else g_setup_err = msg;
   return st;

@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
         "ddm_timing": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                        ctypes.POINTER(ctypes.c_int64)],
         "ddm_factor_bytes": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+        "ddm_norms_noalloc": [_P, ctypes.c_int64, ctypes.c_int, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -281,6 +282,12 @@ def ddm_factor_bytes(ctx):
     b = ctypes.c_int64()
     _check(lib().ddm_factor_bytes(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
     return a.value, b.value
+
+
+def ddm_norms_noalloc(x_dev, n: int, nvec: int, norms_dev, stream=None) -> None:
+    """Allocation-free norms: norms_dev[i] = ||x_i|| for nvec complex128 vectors of length n
+    (x_dev and norms_dev are CUDA tensors; enqueued on the current stream, not synchronised)."""
+    _check(lib().ddm_norms_noalloc(_ptr(x_dev), int(n), int(nvec), _stream(stream), _ptr(norms_dev)), None)
 
 
 # ----------------------------------------------------------------------------- convenience

@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
   const long long fofs = fofs_arr[blockIdx.x];
   const int ldb = ldbs[blockIdx.x];
   const int b = s.ext[0], m = s.ext[1];
-  const int ldm = b | 1;                     // odd leading dimension: conflict-free column access
+  const int njj = (b + 31) / 32;             // 32-column groups per row
+  const int ldm = 32 * njj + 1;              // padded, odd: whole lane groups, conflict-free columns
   cplx<T>* M = (cplx<T>*)smem;               // b x ldm working block
   cplx<T>* colp = M + (long long)b * ldm;    // column p multipliers
   cplx<T>* cC = colp + b;                    // centre of line k
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
   int* perm = (int*)(cNn + b);
   int* cm = perm + b;
   __shared__ int s_piv, s_bad;
-  __shared__ cplx<T> s_inv;
+  __shared__ cplx<T> s_inv, s_app;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   if (tid == 0) s_bad = 0;
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
         }
         if (lane == 0) {
           s_piv = bi;
+          s_app = M[p * ldm + p];
           cplx<T> pv = M[bi * ldm + p];
           if (!(best > (T)0) || !isfinite(best)) { s_bad = 1; s_inv = mk<T>(0, 0); }
           else s_inv = cinv(pv);
@@ -101,25 +103,22 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
       __syncthreads();
       const int r = s_piv;
       const cplx<T> inv = s_inv;
-      // phase A: read row p, row r and column p (after the interchange)
-      cplx<T> ap = mk<T>(0, 0), ar = mk<T>(0, 0), cpv = mk<T>(0, 0);
+      // interchange rows p and r, scale the pivot row, keep the multipliers of column p and
+      // clear column p in the other rows (their final entry there, -f_i / pivot, comes out of
+      // the update below).  Thread j alone reads and writes M[p][j], M[r][j] and M[j][p]; the
+      // old M[p][p], needed as row r's multiplier, was saved by the pivot search.
       if (tid < b) {
-        ap = M[p * ldm + tid];
-        ar = M[r * ldm + tid];
-        int i = tid;
-        cpv = (i == p) ? mk<T>(0, 0) : (i == r ? M[p * ldm + p] : M[i * ldm + p]);
-      }
-      __syncthreads();
-      // phase B: interchange, scale the pivot row, keep the multipliers
-      if (tid < b) {
-        int j = tid;
+        const int j = tid;
+        const cplx<T> ap = M[p * ldm + j];
+        const cplx<T> ar = M[r * ldm + j];
+        colp[j] = (j == p) ? mk<T>(0, 0) : (j == r ? s_app : M[j * ldm + p]);
         M[p * ldm + j] = (j == p) ? inv : ar * inv;
-        if (r != p) M[r * ldm + j] = ap;
-        colp[j] = cpv;
+        if (r != p) M[r * ldm + j] = (j == p) ? mk<T>(0, 0) : ap;
+        if (j != p && j != r) M[j * ldm + p] = mk<T>(0, 0);
       }
       __syncthreads();
-      // phase C: eliminate column p from every other row (warp per row set, lanes over columns,
-      // the pivot row held in registers)
+      // eliminate column p from every other row (warp per row set, lanes over columns, the
+      // pivot row in registers, zero in the padding columns so those stay inert)
       {
         cplx<T> mp[4];
 #pragma unroll
@@ -129,14 +128,14 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
         }
         for (int i = warp; i < b; i += nwarp) {
           if (i == p) continue;
-          const cplx<T> f = colp[i];
+          const cplx<T> f = -colp[i];
+          cplx<T>* Mi = M + i * ldm + lane;
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
-            int j = lane + 32 * jj;
-            if (j < b) {
-              cplx<T> cur = (j == p) ? mk<T>(0, 0) : M[i * ldm + j];
-              cfma(cur, -f, mp[jj]);
-              M[i * ldm + j] = cur;
+            if (jj < njj) {
+              cplx<T> cur = Mi[32 * jj];
+              cfma(cur, f, mp[jj]);
+              Mi[32 * jj] = cur;
             }
           }
         }
@@ -161,7 +160,7 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
 size_t factor_smem_bytes(int b, int ldb, int prec) {
   size_t el = prec == DDM_MIXED ? sizeof(c32) : sizeof(z64);
   (void)ldb;
-  return (size_t)b * (b | 1) * el + 7 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
+  return (size_t)b * (32 * ((b + 31) / 32) + 1) * el + 7 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
 }
 
 // All distinct factors in one launch, one CTA each.  d_reps[f] is a subdomain using factor

@@ -23,6 +23,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -172,13 +173,7 @@ def run_ours(args, rank, world, local_rank):
     avg_launch_ms = solve_ms / max(solve_n, 1)
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9
     pk = peaks()
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "solve2d_traffic.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as fh:
-            tr = json.load(fh)
-        if tr.get("precision") == args.precision and tr.get("kernel_rev") == KERNEL_REV:
-            traffic = tr.get("bytes_per_launch")
+    traffic = solve_traffic(args.precision)
     out = {
         "metric": METRIC, "value": world * 1e3 / ms_per_step, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -261,7 +256,21 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-KERNEL_REV = "solve2d-v2"
+def solve_traffic(precision):
+    """DRAM bytes per k_solve2d launch from the committed ncu summary, or None when the kernel
+    source has changed since the capture (or the capture was of another precision)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_solve2d_2d_heterogeneous_1024.md")
+    src = os.path.join(ROOT, "paper_1807_04180_gb300", "csrc", "solve.cu")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    fields = dict(re.findall(r"^\s+(\w+): (\S+)", txt, re.M))
+    with open(src, "rb") as fh:
+        sha = hashlib.sha1(fh.read()).hexdigest()
+    if fields.get("source_sha1") != sha or fields.get("precision") != precision:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
 
 
 def profile_kernels(args):

@@ -119,8 +119,9 @@ ddm_status ddm_set_medium_host(ddm_ctx *ctx, double omega, const double *c_host)
  * the paper uses a sparse direct solver).  Subdomains whose extended grids
  * carry identical operators share one factor.  Each factor is the block
  * tridiagonal LU in explicit-inverse form: G_k = D_k^{-1} with
- * D_k = T_k - L_k G_{k-1} U_{k-1} over the x-lines (2D) of the subdomain,
- * each D_k inverted by Gauss-Jordan with partial pivoting inside the block.
+ * D_k = T_k - L_k G_{k-1} U_{k-1} over the x-lines (2D) or z-planes (3D) of
+ * the subdomain, each D_k inverted by Gauss-Jordan with partial pivoting
+ * inside the block (in shared memory in 2D, in global memory in 3D).
  * Errors: DDM_E_SINGULAR if a pivot fell below 1e-30 relative to its column,
  * DDM_E_CUDA, DDM_E_STATE.                                                  */
 ddm_status ddm_factor(ddm_ctx *ctx);

@@ -95,7 +95,6 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
   if (!p || !out || !c_dev) return fail(nullptr, DDM_E_INVAL, "null argument");
   *out = nullptr;
   if (p->dim != 2 && p->dim != 3) return fail(nullptr, DDM_E_INVAL, "dim must be 2 or 3");
-  if (p->dim != 2) return fail(nullptr, DDM_E_INVAL, "this build factors 2D subdomains only");
   if (p->overlap < 1 || p->pml < 1) return fail(nullptr, DDM_E_INVAL, "overlap and pml must be >= 1");
   if (!(p->h > 0) || !(omega > 0) || p->sigma0 < 0) return fail(nullptr, DDM_E_INVAL, "h, omega must be > 0, sigma0 >= 0");
   if (p->precision != DDM_FP64 && p->precision != DDM_MIXED) return fail(nullptr, DDM_E_INVAL, "bad precision");
@@ -125,7 +124,8 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     for (int i = 0; i < p->parts[a]; ++i) {
       int64_t w = c->cuts_h[a][i + 1] - c->cuts_h[a][i];
       if (w < 2 * ov || w < 2) { delete c; return fail(nullptr, DDM_E_INVAL, "every part must be at least 2*overlap nodes wide"); }
-      if (a == 0 && w + 2 * e > 128) { delete c; return fail(nullptr, DDM_E_INVAL, "x-extent of a subdomain (own + 2(overlap+pml)) must be <= 128"); }
+      if (d == 2 && a == 0 && w + 2 * e > 128) { delete c; return fail(nullptr, DDM_E_INVAL, "x-extent of a 2D subdomain (own + 2(overlap+pml)) must be <= 128"); }
+      if (d == 3 && a < 2 && w + 2 * e > 96) { delete c; return fail(nullptr, DDM_E_INVAL, "x- and y-extents of a 3D subdomain must be <= 96"); }
     }
   }
   g.nglob = (long long)g.N[0] * g.N[1] * g.N[2];
@@ -299,7 +299,7 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (c->st || true) cudaStreamSynchronize(c->st);
   void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_sidx, c->d_smask, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
-                  c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_V, c->d_Z, c->d_H, c->d_gs};
+                  c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs};
   for (void* q : ptrs) if (q) cudaFree(q);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -381,7 +381,9 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
     if (fid_of_rep[r] < 0) {
       fid_of_rep[r] = (int)reps.size();
       reps.push_back(r);
-      int b = c->subs[r].ext[0], m = c->subs[r].ext[1];
+      // blocks: x-lines in 2D, z-planes in 3D
+      int b = c->dim == 2 ? c->subs[r].ext[0] : c->subs[r].ext[0] * c->subs[r].ext[1];
+      int m = c->dim == 2 ? c->subs[r].ext[1] : c->subs[r].ext[2];
       int ldb = (b + 3) & ~3;
       c->fac_b.push_back(b); c->fac_m.push_back(m); c->fac_ldb.push_back(ldb); c->fac_ofs.push_back(ofs);
       ofs += (long long)m * b * ldb;
@@ -410,7 +412,8 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   cudaEventRecord(e0, c->st);
   {
     TScope ts(c, T_FACTOR);
-    CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
+    if (c->dim == 2) CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
+    else CK(launch_factor3d(c, reps));
   }
   cudaEventRecord(e1, c->st);
   CK(cudaStreamSynchronize(c->st));
@@ -781,9 +784,13 @@ extern "C" ddm_status ddm_factor_bytes(const ddm_ctx* c, int64_t* per_solve, int
   if (!c || !c->factored) return DDM_E_STATE;
   const long long el = (long long)local_elem(c);
   long long ps = 0;
-  for (auto& s : c->subs) {
-    long long b = s.ext[0], m = s.ext[1];
-    ps += (2 * m - 1) * b * b * el;
+  if (c->dim == 2) {
+    for (auto& s : c->subs) {
+      long long b = s.ext[0], m = s.ext[1];
+      ps += (2 * m - 1) * b * b * el;
+    }
+  } else {   // 3D: every factor is streamed once per sweep for all columns that share it
+    for (int f = 0; f < c->nfac; ++f) ps += (2LL * c->fac_m[f] - 1) * c->fac_b[f] * (long long)c->fac_b[f] * el;
   }
   if (per_solve) *per_solve = ps;
   if (stored) *stored = c->fac_elems * el;

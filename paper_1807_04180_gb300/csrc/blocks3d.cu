@@ -1,0 +1,300 @@
+// 3D subdomain factorisation and solves (the local problems of Algorithm 3.1 in 3D).
+//
+// A 3D subdomain operator in natural ordering (x fastest, then y, then z) is block tridiagonal
+// over its z-planes: b = ext_x * ext_y unknowns per plane, m = ext_z planes, diagonal blocks
+// T_k (the in-plane 5-point couplings and the centre), and diagonal couplings L_k = diag(c_zm),
+// U_k = diag(c_zp) between planes.  As in 2D the factor keeps G_k = D_k^{-1},
+// D_k = T_k - L_k G_{k-1} U_{k-1}, column-major with leading dimension ldb; here a block
+// (1444 x 1444 for 38^3 subdomains) lives in global memory (it stays in L2) and is inverted by
+// Gauss-Jordan with partial pivoting, one interchange kernel and one rank-1 update kernel per
+// pivot.  The solve applies the blocks to every right-hand side that shares the factor at once
+// (a GEMM per plane, right-hand sides as columns) with the Schur coupling fused into the
+// operand load and the t / x / U updates fused into the epilogue.
+#include <algorithm>
+#include <vector>
+
+#include "ddm_internal.cuh"
+
+namespace ddm {
+
+struct F3State { int piv; int bad; double app_x, app_y, inv_x, inv_y; };
+
+// ---------------------------------------------------------------------------------- factor
+// D_k into W (row-major b x ldw): W[i][j] = T_k[i][j] - c_zm(i,k) G_{k-1}[i][j] c_zp(j,k-1),
+// G_{k-1} read from the stored column-major factor through the column map cm.
+template <typename T>
+__global__ void k_f3_schur(Geom g, int rep, const cplx<T>* G, long long fofs, int ldb, int k, cplx<T>* W, int ldw,
+                           const int* cm) {
+  const SubDesc& s = g.subs[rep];
+  const int ex = s.ext[0], ey = s.ext[1], ez = s.ext[2];
+  const int b = ex * ey;
+  const long long len = (long long)b * ez;
+  const cplx<T>* lc = (const cplx<T>*)g.lcoef + s.vofs * 7;   // C, x-, x+, y-, y+, z-, z+
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)b * b;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / b), j = (int)(idx - (long long)i * b);
+    cplx<T> d = mk<T>(0, 0);
+    const long long oi = (long long)k * b + i;
+    if (k > 0) {
+      const cplx<T> gij = G[fofs + ((long long)(k - 1) * b + j) * ldb + i];
+      const long long oj = (long long)(k - 1) * b + j;
+      d = -(lc[5 * len + oi] * gij * lc[6 * len + oj]);
+    }
+    if (j == i) d = d + lc[oi];
+    const int xi = i % ex, yi = i / ex;
+    if (j == i + 1 && xi + 1 < ex) d = d + lc[2 * len + oi];
+    if (j == i - 1 && xi > 0) d = d + lc[1 * len + oi];
+    if (j == i + ex && yi + 1 < ey) d = d + lc[4 * len + oi];
+    if (j == i - ex && yi > 0) d = d + lc[3 * len + oi];
+    W[(long long)i * ldw + j] = d;
+  }
+  (void)cm;
+}
+
+// pivot of column p (rows >= p), then the interchange of rows p and r, scaling of the pivot
+// row, the multipliers of column p (colp) and clearing of column p in the other rows
+template <typename T>
+__global__ void k_f3_pivot(int b, int p, cplx<T>* W, int ldw, cplx<T>* colp, int* perm, F3State* st, int* err) {
+  __shared__ T sbest[32];
+  __shared__ int sidx[32];
+  __shared__ int s_r;
+  __shared__ cplx<T> s_inv, s_app;
+  T best = (T)-1;
+  int bi = p;
+  for (int i = p + threadIdx.x; i < b; i += blockDim.x) {
+    const T a = cabs2(W[(long long)i * ldw + p]);
+    if (a > best) { best = a; bi = i; }
+  }
+  for (int o = 16; o; o >>= 1) {
+    const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { sbest[threadIdx.x >> 5] = best; sidx[threadIdx.x >> 5] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sbest[w] > best || (sbest[w] == best && sidx[w] < bi)) { best = sbest[w]; bi = sidx[w]; }
+    s_r = bi;
+    s_app = W[(long long)p * ldw + p];
+    if (!(best > (T)0) || !isfinite(best)) { atomicOr(err, ERRBIT_SINGULAR); s_inv = mk<T>(0, 0); }
+    else s_inv = cinv(W[(long long)bi * ldw + p]);
+    perm[p] = bi;
+    st->piv = bi;
+  }
+  __syncthreads();
+  const int r = s_r;
+  const cplx<T> inv = s_inv, app = s_app;
+  // thread j alone touches W[p][j], W[r][j] and W[j][p]
+  for (int j = threadIdx.x; j < b; j += blockDim.x) {
+    const cplx<T> ap = W[(long long)p * ldw + j];
+    const cplx<T> ar = W[(long long)r * ldw + j];
+    colp[j] = (j == p) ? mk<T>(0, 0) : (j == r ? app : W[(long long)j * ldw + p]);
+    W[(long long)p * ldw + j] = (j == p) ? inv : ar * inv;
+    if (r != p) W[(long long)r * ldw + j] = (j == p) ? mk<T>(0, 0) : ap;
+    if (j != p && j != r) W[(long long)j * ldw + p] = mk<T>(0, 0);
+  }
+}
+
+// W[i][j] -= colp[i] W[p][j] for every row i != p (rank-1 update, column p already cleared)
+template <typename T>
+__global__ void k_f3_update(int b, int p, cplx<T>* W, int ldw, const cplx<T>* colp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b) return;
+  const cplx<T> mp = W[(long long)p * ldw + j];
+  for (int i = blockIdx.y; i < b; i += gridDim.y) {
+    if (i == p) continue;
+    cplx<T> cur = W[(long long)i * ldw + j];
+    cfma(cur, -colp[i], mp);
+    W[(long long)i * ldw + j] = cur;
+  }
+}
+
+// G_k (column-major, ld ldb) from W with the column interchanges undone
+template <typename T>
+__global__ void k_f3_store(int b, const cplx<T>* W, int ldw, const int* cm, cplx<T>* G, long long gofs, int ldb) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)b * ldb;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / ldb), i = (int)(idx - (long long)j * ldb);
+    G[gofs + idx] = i < b ? W[(long long)i * ldw + cm[j]] : mk<T>(0, 0);
+  }
+}
+
+__global__ void k_f3_colmap(int b, const int* perm, int* cm) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    for (int j = 0; j < b; ++j) cm[j] = j;
+    for (int p = b - 1; p >= 0; --p) { const int q = perm[p]; const int t = cm[p]; cm[p] = cm[q]; cm[q] = t; }
+  }
+}
+
+template <typename T>
+static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
+  cudaError_t e = cudaSuccess;
+  int bmax = 0;
+  for (size_t f = 0; f < reps.size(); ++f) bmax = std::max(bmax, c->fac_b[f]);
+  const int ldw = bmax;
+  cplx<T>* W = nullptr;
+  cplx<T>* colp = nullptr;
+  int *perm = nullptr, *cm = nullptr;
+  F3State* st = nullptr;
+  if ((e = cudaMalloc((void**)&W, sizeof(cplx<T>) * (size_t)bmax * ldw)) != cudaSuccess) return e;
+  if ((e = cudaMalloc((void**)&colp, sizeof(cplx<T>) * bmax)) != cudaSuccess) return e;
+  if ((e = cudaMalloc((void**)&perm, sizeof(int) * bmax)) != cudaSuccess) return e;
+  if ((e = cudaMalloc((void**)&cm, sizeof(int) * bmax)) != cudaSuccess) return e;
+  if ((e = cudaMalloc((void**)&st, sizeof(F3State))) != cudaSuccess) return e;
+  cplx<T>* G = (cplx<T>*)c->d_G;
+  for (size_t f = 0; f < reps.size(); ++f) {
+    const int b = c->fac_b[f], m = c->fac_m[f], ldb = c->fac_ldb[f];
+    const long long fofs = c->fac_ofs[f];
+    for (int k = 0; k < m; ++k) {
+      ++c->nlaunch;
+      k_f3_schur<T><<<1216, 256, 0, c->st>>>(c->g, reps[f], G, fofs, ldb, k, W, ldw, cm);
+      for (int p = 0; p < b; ++p) {
+        c->nlaunch += 2;
+        k_f3_pivot<T><<<1, 1024, 0, c->st>>>(b, p, W, ldw, colp, perm, st, c->d_err);
+        dim3 gu((b + 127) / 128, 152);
+        k_f3_update<T><<<gu, 128, 0, c->st>>>(b, p, W, ldw, colp);
+      }
+      c->nlaunch += 2;
+      k_f3_colmap<<<1, 1, 0, c->st>>>(b, perm, cm);
+      k_f3_store<T><<<1216, 256, 0, c->st>>>(b, W, ldw, cm, G, fofs + (long long)k * b * ldb, ldb);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+    }
+  }
+  cudaStreamSynchronize(c->st);
+  cudaFree(W); cudaFree(colp); cudaFree(perm); cudaFree(cm); cudaFree(st);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+cudaError_t launch_factor3d(ddm_ctx* c, const std::vector<int>& reps) {
+  return c->prec == DDM_MIXED ? factor3d_t<float>(c, reps) : factor3d_t<double>(c, reps);
+}
+
+// ---------------------------------------------------------------------------------- solve
+// One plane step for the columns (subdomain, right-hand side) of one factor group:
+//   forward  (pass 0): C = G_k Y,  Y[j][q] = src_q[k b + j] - c_zm(j,k) out_q[(k-1) b + j]
+//                      out_q[k b + i] = C[i][q]; at k = m-1 also U_q += C
+//   backward (pass 1): C = G_k Z,  Z[j][q] = c_zp(j,k) out_q[(k+1) b + j]
+//                      x = out_q[k b + i] - C[i][q]; out_q = x; U_q += x
+// colofs[q] = element offset of column q's local vector (subdomain offset + rhs * ltotal).
+constexpr int G3_BM = 64, G3_BN = 64, G3_BK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm3d(const cplx<T>* __restrict__ G, long long gofs, int ldb, int b,
+                                               const cplx<T>* __restrict__ cS, const cplx<T>* __restrict__ cN,
+                                               int pass, int k, int m, const long long* __restrict__ colofs, int ncol,
+                                               const cplx<T>* __restrict__ src, cplx<T>* out, cplx<T>* U) {
+  __shared__ cplx<T> As[G3_BK][G3_BM + 1];
+  __shared__ cplx<T> Bs[G3_BK][G3_BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;            // 16 x 16 threads, 4 x 4 outputs each
+  const int i0 = blockIdx.x * G3_BM, q0 = blockIdx.y * G3_BN;
+  cplx<T> acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = mk<T>(0, 0);
+  const cplx<T>* Gk = G + gofs + (long long)k * b * ldb;
+  for (int j0 = 0; j0 < b; j0 += G3_BK) {
+    // A tile: G_k[i0 .. i0+63][j0 .. j0+15] (column-major: contiguous in i)
+    for (int t = tid; t < G3_BM * G3_BK; t += 256) {
+      const int ii = t % G3_BM, jj = t / G3_BM;
+      const int i = i0 + ii, j = j0 + jj;
+      As[jj][ii] = (i < b && j < b) ? Gk[(long long)j * ldb + i] : mk<T>(0, 0);
+    }
+    // B tile: the block's right-hand side for columns q0 .. q0+63, rows j0 .. j0+15
+    for (int t = tid; t < G3_BK * G3_BN; t += 256) {
+      const int jj = t % G3_BK, qq = t / G3_BK;
+      const int j = j0 + jj, q = q0 + qq;
+      cplx<T> v = mk<T>(0, 0);
+      if (j < b && q < ncol) {
+        const long long base = colofs[q];
+        if (pass == 0) {
+          v = src[base + (long long)k * b + j];
+          if (k > 0) v = v - cS[(long long)k * b + j] * out[base + (long long)(k - 1) * b + j];
+        } else {
+          v = cN[(long long)k * b + j] * out[base + (long long)(k + 1) * b + j];
+        }
+      }
+      Bs[jj][qq] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < G3_BK; ++jj) {
+      cplx<T> av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[jj][ty + 16 * a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[jj][tx + 16 * c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cfma(acc[a][c], av[a], bv[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a;
+    if (i >= b) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int q = q0 + tx + 16 * c;
+      if (q >= ncol) continue;
+      const long long o = colofs[q] + (long long)k * b + i;
+      cplx<T> v = acc[a][c];
+      if (pass == 1) v = out[o] - v;
+      out[o] = v;
+      if (U && (pass == 1 || k == m - 1)) U[o] = U[o] + v;
+    }
+  }
+}
+
+template <typename T>
+static cudaError_t solve3d_t(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
+  // columns grouped by factor
+  std::vector<std::vector<long long>> cols(c->nfac);
+  std::vector<int> rep(c->nfac, -1);
+  for (int r = 0; r < nrhs; ++r)
+    for (int s = 0; s < c->g.nsub; ++s) {
+      cols[c->subs[s].fid].push_back(c->subs[s].vofs + (long long)r * c->g.ltotal);
+      if (rep[c->subs[s].fid] < 0) rep[c->subs[s].fid] = s;
+    }
+  cudaError_t e = cudaSuccess;
+  for (int f = 0; f < c->nfac; ++f) {
+    const int ncol = (int)cols[f].size();
+    if (!ncol) continue;
+    if ((size_t)ncol > c->col3d_cap) {
+      if (c->d_col3d) cudaFree(c->d_col3d);
+      c->d_col3d = nullptr;
+      if ((e = cudaMalloc((void**)&c->d_col3d, sizeof(long long) * ncol)) != cudaSuccess) return e;
+      c->col3d_cap = ncol;
+    }
+    if ((e = cudaMemcpyAsync(c->d_col3d, cols[f].data(), sizeof(long long) * ncol, cudaMemcpyHostToDevice, c->st)) !=
+        cudaSuccess)
+      return e;
+    const SubDesc& s = c->subs[rep[f]];
+    const int b = c->fac_b[f], m = c->fac_m[f], ldb = c->fac_ldb[f];
+    const long long len = (long long)b * m;
+    const cplx<T>* lc = (const cplx<T>*)c->d_lcoef + s.vofs * 7;
+    dim3 grid((b + G3_BM - 1) / G3_BM, (ncol + G3_BN - 1) / G3_BN);
+    for (int i = 0; i < 2 * m - 1; ++i) {
+      const int pass = i < m ? 0 : 1;
+      const int k = pass == 0 ? i : 2 * m - 2 - i;
+      ++c->nlaunch;
+      k_gemm3d<T><<<grid, 256, 0, c->st>>>((const cplx<T>*)c->d_G, c->fac_ofs[f], ldb, b, lc + 5 * len, lc + 6 * len,
+                                           pass, k, m, c->d_col3d, ncol, (const cplx<T>*)src, (cplx<T>*)out,
+                                           (cplx<T>*)U);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the column list is reused by the next group: wait until these launches have read it
+    if (f + 1 < c->nfac) cudaStreamSynchronize(c->st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_solve3d(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
+  return c->prec == DDM_MIXED ? solve3d_t<float>(c, src, out, U, nrhs) : solve3d_t<double>(c, src, out, U, nrhs);
+}
+
+}  // namespace ddm

@@ -185,6 +185,9 @@ struct ddm_ctx {
   ddm::z64* d_Z = nullptr;
   ddm::z64* d_H = nullptr;       // (m+1) x m column major
   ddm::z64* d_gs = nullptr;      // Givens: cs[m], sn[m], g[m+1], y[m]
+  // 3D solves: column offsets of the right-hand sides sharing a factor
+  long long* d_col3d = nullptr;
+  size_t col3d_cap = 0;
   // kernels launched by this context (ddm_kernel_launches)
   long long nlaunch = 0;
   // timing
@@ -223,4 +226,6 @@ cudaError_t launch_lsq_update(ddm_ctx* c, int j, int m, z64* H, z64* gs, const z
 cudaError_t launch_copy_scaled(ddm_ctx* c, const z64* src, double s, z64* dst, long long n);
 cudaError_t launch_axpy(ddm_ctx* c, double s, const z64* w, z64* x, long long n);
 int ring_slots(const ddm_ctx* c);
+cudaError_t launch_factor3d(ddm_ctx* c, const std::vector<int>& reps);
+cudaError_t launch_local_solve3d(ddm_ctx* c, const void* src, void* out, void* U, int nrhs);
 }  // namespace ddm

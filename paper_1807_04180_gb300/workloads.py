@@ -213,6 +213,22 @@ def tiny_2d(seed: int = 0, n: int = 12, parts=(2, 2), ov: int = 1, npml: int = 3
     return Workload("tiny2d", shape, h, cuts, ov, npml, 10.0, 2.0, 2 * math.pi * k_over_2pi, c, f)
 
 
+def tiny_3d(seed: int = 0, n: int = 12, parts=(2, 2, 2), ov: int = 1, npml: int = 3,
+            medium: str = "gauss", k_over_2pi: float = 1.5) -> Workload:
+    """Small 3D case the oracle solves directly: n^3 interior, parts subdomains."""
+    h = 1.0 / n
+    e = ov + npml
+    shape = (n, n, n)
+    if medium == "const":
+        c = constant_medium(shape, e)
+    else:
+        c = gaussian_sum_medium(shape, h, e, seed, n_bumps=4, cmin=1.0, cmax=2.0)
+    rng = np.random.default_rng(seed + 2000)
+    f = gaussian_source(shape, h, e, rng.uniform(0.25, 0.75, 3), 2 * h)[None]
+    cuts = tuple(uniform_cuts(n, p) for p in parts)
+    return Workload("tiny3d", shape, h, cuts, ov, npml, 10.0, 2.0, 2 * math.pi * k_over_2pi, c, f)
+
+
 def constant_2d_160(seed: int = 1) -> Workload:
     """2D constant medium, k = 2 pi 10 on [0,1]^2, 160^2 interior, 4x4 subdomains of 40^2,
     2-cell overlap, 10-cell PML (sigma0 = 50, quadratic), Gaussian source of width 2h at a

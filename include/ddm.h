@@ -210,6 +210,13 @@ ddm_status ddm_timing(ddm_ctx *ctx, int enable, int reset, double *out_ms, int64
  * reset); reset != 0 clears the counter after reading it.                    */
 ddm_status ddm_kernel_launches(ddm_ctx *ctx, int64_t *count, int reset);
 
+/* Autotuner record of the 2D local solve: the first local solve of nrhs > 1
+ * right-hand sides on a context times every right-hand-side grouping per CTA
+ * (1, 2, 4, 8; 8 only in complex64) on its own input and keeps the fastest
+ * for that nrhs.  Fills up to cap entries (nrhs, grouping, device ms) and
+ * sets *count to the number recorded (any output may be NULL).              */
+ddm_status ddm_autotune_log(const ddm_ctx *ctx, int cap, int *nrhs, int *nr, float *ms, int *count);
+
 /* Bytes of subdomain factors read by one batched local solve of one
  * right-hand side per subdomain (each distinct factor streamed twice, once
  * per sweep, per subdomain using it), and bytes of factor storage.          */

@@ -239,7 +239,8 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
   const size_t le = local_elem(c);
   int maxlen = 0;
   for (auto& s : c->subs) maxlen = std::max(maxlen, s.ext[0] * s.ext[1] * s.ext[2]);
-  c->npart = std::max<long long>((long long)R * g.nsub * ((maxlen + 255) / 256), 304LL * 2 * 130);
+  c->npart = std::max<long long>((long long)R * g.nsub * ((maxlen + 127) / 128 + 1),
+                                  (long long)R * 304LL * 2 * 122);
   int* d_tdesc = nullptr;
 #define ALLOC(ptr, bytes) CK(cudaMalloc((void**)&(ptr), (bytes)))
   ddm_status st = DDM_OK;
@@ -297,6 +298,9 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
 extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (!c) return DDM_OK;
   if (c->st || true) cudaStreamSynchronize(c->st);
+  if (c->h_bscal) cudaFreeHost(c->h_bscal);
+  if (c->d_bscal) cudaFree(c->d_bscal);
+  if (c->d_jr) cudaFree(c->d_jr);
   void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_sidx, c->d_smask, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
                   c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs};
@@ -563,88 +567,138 @@ static double host_norm(ddm_ctx* c, const z64* x, ddm_status* st) {
   return std::sqrt(c->h_scal[32]);
 }
 
-static ddm_status ensure_krylov(ddm_ctx* c, int m) {
-  if (c->kry_m >= m) return DDM_OK;
-  if (c->d_V) { cudaFree(c->d_V); cudaFree(c->d_Z); cudaFree(c->d_H); cudaFree(c->d_gs); }
+static ddm_status ensure_krylov(ddm_ctx* c, int m, int nb) {
+  if (c->kry_m >= m && c->kry_nb >= nb) return DDM_OK;
+  void* old[] = {c->d_V, c->d_Z, c->d_H, c->d_gs, c->d_bscal, c->d_jr};
+  for (void* q : old) if (q) cudaFree(q);
+  if (c->h_bscal) cudaFreeHost(c->h_bscal);
   c->d_V = c->d_Z = c->d_H = c->d_gs = nullptr;
-  c->kry_m = 0;
-  CK(cudaMalloc((void**)&c->d_V, sizeof(z64) * c->g.nglob * (m + 1)));
-  CK(cudaMalloc((void**)&c->d_Z, sizeof(z64) * c->g.nglob * m));
-  CK(cudaMalloc((void**)&c->d_H, sizeof(z64) * (m + 1) * m));
-  CK(cudaMalloc((void**)&c->d_gs, sizeof(z64) * (5 * m + 4)));
+  c->d_bscal = nullptr; c->h_bscal = nullptr; c->d_jr = nullptr;
+  c->kry_m = c->kry_nb = 0;
+  const long long n = c->g.nglob;
+  CK(cudaMalloc((void**)&c->d_V, sizeof(z64) * n * (m + 1) * nb));
+  CK(cudaMalloc((void**)&c->d_Z, sizeof(z64) * n * m * nb));
+  CK(cudaMalloc((void**)&c->d_H, sizeof(z64) * (m + 1) * m * nb));
+  CK(cudaMalloc((void**)&c->d_gs, sizeof(z64) * (5 * m + 4) * nb));
+  CK(cudaMalloc((void**)&c->d_bscal, sizeof(double) * 4 * nb));
+  CK(cudaMallocHost((void**)&c->h_bscal, sizeof(double) * 4 * nb));
+  CK(cudaMalloc((void**)&c->d_jr, sizeof(int) * nb));
   c->kry_m = m;
+  c->kry_nb = nb;
   return DDM_OK;
 }
 
-// Flexible GMRES(m) for A x = b (one right-hand side), right-preconditioned by M_K.
-static ddm_status fgmres_one(ddm_ctx* c, const z64* b, z64* x, double tol, int max_it, int K, int m, ddm_info* info) {
+// Flexible GMRES(m) for A x_r = b_r, r < nb, right-preconditioned by M_K (Section 4.2.2).
+// The nb recurrences advance together: one nb-wide preconditioner application (the local
+// solves stream each factor block once for up to 8 right-hand sides) and one nb-wide global
+// operator per iteration; Arnoldi, Givens and the least-squares update are per right-hand side.
+// A right-hand side that has converged keeps its iterate; later cycles run it on a zero basis.
+static ddm_status fgmres_batch(ddm_ctx* c, const z64* b, z64* x, int nb, double tol, int max_it, int K, int m,
+                               ddm_info* info) {
   const long long n = c->g.nglob;
-  ddm_status st;
-  CKS(ensure_krylov(c, m));
-  double bnorm = host_norm(c, b, &st);
-  if (st != DDM_OK) return st;
-  CK(cudaMemsetAsync(x, 0, sizeof(z64) * n, c->st));
-  if (bnorm == 0.0) { if (info) { info->converged = 1; info->rel_residual = 0; } return DDM_OK; }
+  CKS(ensure_krylov(c, m, nb));
+  double* d_nrm2 = c->d_bscal;         // nb: squared norms
+  double* d_est = c->d_bscal + nb;     // nb: residual estimates
+  double* d_sc = c->d_bscal + 2 * nb;  // nb: scale factors
+  double* h = c->h_bscal;
   z64* V = c->d_V;
   z64* Z = c->d_Z;
   z64* H = c->d_H;
   z64* gs = c->d_gs;
-  z64* coef = gs + 4 * m + 2;
+  const int GSZ = 5 * m + 4;
+  // coefficient scratch for the Gram-Schmidt passes: nb x (m+1), after the gs blocks' y part
+  z64* coef = nullptr;
+  CK(cudaMalloc((void**)&coef, sizeof(z64) * (m + 1) * nb));
+  auto cleanup = [&]() { cudaFree(coef); };
+  auto batch_norms = [&](const z64* v) -> ddm_status {
+    int nblk = 0;
+    CK(launch_norm2_partial(c, v, n, nb, c->d_part, &nblk));
+    CK(launch_sum_partials(c, c->d_part, nblk, nb, d_nrm2));
+    CK(cudaMemcpyAsync(h, d_nrm2, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return DDM_OK;
+  };
+  std::vector<double> bnorm(nb), est(nb, 1.0);
+  std::vector<char> conv(nb, 0);
+  { ddm_status st = batch_norms(b); if (st != DDM_OK) { cleanup(); return st; } }
+  for (int r = 0; r < nb; ++r) { bnorm[r] = std::sqrt(h[r]); if (bnorm[r] == 0.0) { conv[r] = 1; est[r] = 0; } }
+  CK(cudaMemsetAsync(x, 0, sizeof(z64) * n * nb, c->st));
   int it = 0, steps = 0;
-  double est = 1.0;
-  bool conv = false;
-  while (it < max_it && !conv) {
+  auto all_done = [&]() { for (int r = 0; r < nb; ++r) if (!conv[r]) return false; return true; };
+  while (it < max_it && !all_done()) {
     {
       TScope ts(c, T_GLOBAL);
-      CK(launch_global_apply(c, x, c->d_gr, b, 1));
+      CK(launch_global_apply(c, x, c->d_gr, b, nb));
     }
-    double beta = host_norm(c, c->d_gr, &st);
-    if (st != DDM_OK) return st;
-    est = beta / bnorm;
-    if (est <= tol) { conv = true; break; }
-    CK(launch_copy_scaled(c, c->d_gr, 1.0 / beta, V, n));
-    CK(cudaMemsetAsync(gs, 0, sizeof(z64) * (5 * m + 4), c->st));
-    CK(cudaMemsetAsync(H, 0, sizeof(z64) * (m + 1) * m, c->st));
-    z64 g0 = mk<double>(beta, 0.0);
-    CK(cudaMemcpyAsync(gs + 2 * m, &g0, sizeof(z64), cudaMemcpyHostToDevice, c->st));
+    { ddm_status st = batch_norms(c->d_gr); if (st != DDM_OK) { cleanup(); return st; } }
+    std::vector<double> beta(nb), scale(nb);
+    for (int r = 0; r < nb; ++r) {
+      beta[r] = std::sqrt(h[r]);
+      if (!conv[r]) { est[r] = beta[r] / bnorm[r]; if (est[r] <= tol) conv[r] = 1; }
+      scale[r] = (!conv[r] && beta[r] > 0) ? 1.0 / beta[r] : 0.0;
+    }
+    if (all_done()) break;
+    CK(cudaMemcpyAsync(d_sc, scale.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, c->st));
+    CK(launch_scale_vec_b(c, nb, c->d_gr, d_sc, V, n));
+    CK(cudaMemsetAsync(gs, 0, sizeof(z64) * GSZ * nb, c->st));
+    CK(cudaMemsetAsync(H, 0, sizeof(z64) * (m + 1) * m * nb, c->st));
+    std::vector<z64> g0(nb);
+    for (int r = 0; r < nb; ++r) g0[r] = mk<double>(conv[r] ? 0.0 : beta[r], 0.0);
+    for (int r = 0; r < nb; ++r)
+      CK(cudaMemcpyAsync(gs + (long long)r * GSZ + 2 * m, &g0[r], sizeof(z64), cudaMemcpyHostToDevice, c->st));
+    std::vector<char> active(nb);
+    std::vector<int> jr(nb, 0);
+    for (int r = 0; r < nb; ++r) active[r] = !conv[r];
     int j = 0;
     for (; j < m && it < max_it; ++j) {
-      z64* vj = V + (long long)j * n;
-      z64* zj = Z + (long long)j * n;
-      z64* w = V + (long long)(j + 1) * n;
-      CKS(run_steps(c, vj, 1, K, zj, nullptr, nullptr));
+      z64* vj = V + (long long)j * nb * n;
+      z64* zj = Z + (long long)j * nb * n;
+      z64* w = V + (long long)(j + 1) * nb * n;
+      { ddm_status st = run_steps(c, vj, nb, K, zj, nullptr, nullptr); if (st != DDM_OK) { cleanup(); return st; } }
       steps += K;
       {
         TScope ts(c, T_GLOBAL);
-        CK(launch_global_apply(c, zj, w, nullptr, 1));
+        CK(launch_global_apply(c, zj, w, nullptr, nb));
       }
       {
         TScope ts(c, T_KRYLOV);
         for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
           int nblk = 0;
-          CK(launch_dots(c, V, j + 1, w, n, c->d_part, &nblk));
-          CK(launch_arnoldi_coef(c, c->d_part, nblk, j + 1, H + (long long)j * (m + 1), coef, pass == 0));
-          CK(launch_sub_axpy(c, V, j + 1, coef, w, n));
+          CK(launch_dots_b(c, V, nb, j + 1, w, n, c->d_part, &nblk));
+          CK(launch_arnoldi_coef_b(c, c->d_part, nblk, j + 1, nb, H, j, m, coef, pass == 0));
+          CK(launch_sub_axpy_b(c, V, nb, j + 1, coef, m, w, n));
         }
         int nblk = 0;
-        CK(launch_norm2_partial(c, w, n, 1, c->d_part, &nblk));
-        CK(launch_sum_partials(c, c->d_part, nblk, 1, c->d_scal + 40));
-        CK(launch_givens(c, j, m, c->d_scal + 40, H, gs, c->d_scal + 41));
-        CK(launch_scale(c, w, gs + 3 * m + 1, w, n));
+        CK(launch_norm2_partial(c, w, n, nb, c->d_part, &nblk));
+        CK(launch_sum_partials(c, c->d_part, nblk, nb, d_nrm2));
+        CK(launch_givens_b(c, nb, j, m, d_nrm2, H, gs, d_est));
+        CK(launch_scale_b(c, nb, w, gs, m, n));
       }
-      CK(cudaMemcpyAsync(c->h_scal + 41, c->d_scal + 41, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(h + nb, d_est, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
       ++it;
-      est = c->h_scal[41] / bnorm;
-      if (!(est == est)) return fail(c, DDM_E_NOCONV, "non-finite residual estimate in FGMRES");
-      if (est <= tol) { ++j; conv = true; break; }
+      bool pending = false;
+      for (int r = 0; r < nb; ++r) {
+        if (!active[r] || jr[r] > 0) continue;
+        est[r] = h[nb + r] / bnorm[r];
+        if (!(est[r] == est[r])) { cleanup(); return fail(c, DDM_E_NOCONV, "non-finite residual estimate in FGMRES"); }
+        if (est[r] <= tol) { conv[r] = 1; jr[r] = j + 1; }
+        else pending = true;
+      }
+      if (!pending) { ++j; break; }
     }
+    for (int r = 0; r < nb; ++r) if (active[r] && jr[r] == 0) jr[r] = j;
+    CK(cudaMemcpyAsync(c->d_jr, jr.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st));
     {
       TScope ts(c, T_KRYLOV);
-      CK(launch_lsq_update(c, j, m, H, gs, Z, x, n));
+      CK(launch_lsq_update_b(c, nb, c->d_jr, m, H, gs, Z, x, n));
     }
+    CK(cudaStreamSynchronize(c->st));   // jr (host vector) must outlive the copy above
   }
-  if (info) { info->iters += it; info->ddm_steps += steps; info->rel_residual_est = est; }
+  cleanup();
+  double worst = 0;
+  for (int r = 0; r < nb; ++r) worst = std::max(worst, est[r]);
+  if (info) { info->iters += it; info->ddm_steps += steps; info->rel_residual_est = worst; }
   return DDM_OK;
 }
 
@@ -712,8 +766,11 @@ static ddm_status solve_impl(ddm_ctx* c, const void* f_dev, void* u_dev, int nrh
   for (int r = 0; r < nrhs; ++r) {
     const z64* b = c->d_gb + (long long)r * n;
     z64* x = (z64*)u_dev + (long long)r * n;
-    if (mode == DDM_FGMRES) CKS(fgmres_one(c, b, x, tol, max_it, K, restart, &loc));
-    else CKS(stepping_one(c, b, x, tol, max_it, &loc));
+    if (mode == DDM_FGMRES) {
+      if (r == 0) CKS(fgmres_batch(c, c->d_gb, (z64*)u_dev, nrhs, tol, max_it, K, restart, &loc));
+    } else {
+      CKS(stepping_one(c, b, x, tol, max_it, &loc));
+    }
     double nr[2];
     CKS(ddm_residual(c, b, x, c->d_gr, 1, nr));
     double rel = nr[1] > 0 ? nr[0] / nr[1] : 0.0;
@@ -777,6 +834,18 @@ extern "C" ddm_status ddm_timing(ddm_ctx* c, int enable, int reset, double* out_
   if (out_launches) for (int i = 0; i < T_NSLOT; ++i) out_launches[i] = c->t_n[i];
   if (reset) for (int i = 0; i < T_NSLOT; ++i) { c->t_ms[i] = 0; c->t_n[i] = 0; }
   c->timing = enable != 0;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_autotune_log(const ddm_ctx* c, int cap, int* nrhs, int* nr, float* ms, int* count) {
+  if (!c) return DDM_E_INVAL;
+  const int n = (int)c->tune_log.size();
+  if (count) *count = n;
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (nrhs) nrhs[i] = c->tune_log[i].nrhs;
+    if (nr) nr[i] = c->tune_log[i].nr;
+    if (ms) ms[i] = c->tune_log[i].ms;
+  }
   return DDM_OK;
 }
 

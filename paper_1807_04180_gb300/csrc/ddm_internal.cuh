@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ddm.h"
@@ -180,7 +182,10 @@ struct ddm_ctx {
   ddm::z64* d_hostbuf = nullptr; // staging for ddm_solve_host: f then u, max_rhs wide each
   double* d_chost = nullptr;     // staging for ddm_set_medium_host
   // Krylov workspace (allocated on first FGMRES solve)
-  int kry_m = 0;
+  int kry_m = 0, kry_nb = 0;
+  double* d_bscal = nullptr;     // batched Krylov scalars: 4 x nb doubles
+  double* h_bscal = nullptr;     // pinned mirror
+  int* d_jr = nullptr;           // per right-hand side basis length of the current cycle
   ddm::z64* d_V = nullptr;
   ddm::z64* d_Z = nullptr;
   ddm::z64* d_H = nullptr;       // (m+1) x m column major
@@ -188,6 +193,10 @@ struct ddm_ctx {
   // 3D solves: column offsets of the right-hand sides sharing a factor
   long long* d_col3d = nullptr;
   size_t col3d_cap = 0;
+  // autotuned right-hand sides per CTA of the 2D local solve, per nrhs, and the timings taken
+  std::map<int, int> tuned_nr;
+  struct TuneRec { int nrhs, nr; float ms; };
+  std::vector<TuneRec> tune_log;
   // kernels launched by this context (ddm_kernel_launches)
   long long nlaunch = 0;
   // timing
@@ -225,6 +234,15 @@ cudaError_t launch_scale(ddm_ctx* c, const z64* x, const z64* s, z64* dst, long 
 cudaError_t launch_lsq_update(ddm_ctx* c, int j, int m, z64* H, z64* gs, const z64* Z, z64* x, long long n);
 cudaError_t launch_copy_scaled(ddm_ctx* c, const z64* src, double s, z64* dst, long long n);
 cudaError_t launch_axpy(ddm_ctx* c, double s, const z64* w, z64* x, long long n);
+cudaError_t launch_dots_b(ddm_ctx* c, const z64* V, int nb, int nv, const z64* w, long long n, double* part, int* nblocks);
+cudaError_t launch_arnoldi_coef_b(ddm_ctx* c, const double* part, int nblocks, int nv, int nb, z64* H, int j, int m,
+                                  z64* coef, int first);
+cudaError_t launch_sub_axpy_b(ddm_ctx* c, const z64* V, int nb, int nv, const z64* coef, int m, z64* w, long long n);
+cudaError_t launch_givens_b(ddm_ctx* c, int nb, int j, int m, const double* nrm2, z64* H, z64* gs, double* out_est);
+cudaError_t launch_scale_b(ddm_ctx* c, int nb, z64* w, const z64* gs, int m, long long n);
+cudaError_t launch_scale_vec_b(ddm_ctx* c, int nb, const z64* src, const double* s, z64* dst, long long n);
+cudaError_t launch_lsq_update_b(ddm_ctx* c, int nb, const int* d_jr, int m, const z64* H, z64* gs, const z64* Z, z64* x,
+                                long long n);
 int ring_slots(const ddm_ctx* c);
 cudaError_t launch_factor3d(ddm_ctx* c, const std::vector<int>& reps);
 cudaError_t launch_local_solve3d(ddm_ctx* c, const void* src, void* out, void* U, int nrhs);

@@ -275,3 +275,207 @@ cudaError_t launch_lsq_update(ddm_ctx* c, int j, int m, z64* H, z64* gs, const z
 }
 
 }  // namespace ddm
+
+// ===========================================================================
+// Batched variants: nb independent Krylov recurrences advanced together.  Basis vector v of
+// right-hand side r is V + (v nb + r) n; right-hand side r's Hessenberg matrix is
+// H + r (m+1) m (column-major), its Givens/LSQ scratch gs + r GSZ, GSZ = 5 m + 4.
+// ===========================================================================
+namespace ddm {
+
+template <int NV>
+__global__ void k_dots_b(const z64* V, int nb, int v0, int nv, const z64* w, long long n, double* part, int nvtot) {
+  __shared__ double sh[32];
+  const int r = blockIdx.z;
+  const z64* wr = w + (long long)r * n;
+  z64 acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = mk<double>(0, 0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const z64 wi = wr[i];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (v < nv) cfma_conj(acc[v], V[((long long)(v0 + v) * nb + r) * n + i], wi);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v >= nv) break;
+    const double re = block_sum(acc[v].x, sh);
+    const double im = block_sum(acc[v].y, sh);
+    if (threadIdx.x == 0) {
+      double* p = part + (((long long)r * gridDim.x + blockIdx.x) * nvtot + v0 + v) * 2;
+      p[0] = re;
+      p[1] = im;
+    }
+  }
+}
+
+cudaError_t launch_dots_b(ddm_ctx* c, const z64* V, int nb, int nv, const z64* w, long long n, double* part, int* nblocks) {
+  for (int v0 = 0; v0 < nv; v0 += 8) {
+    ++c->nlaunch;
+    k_dots_b<8><<<dim3(RED_BLOCKS, 1, nb), 256, 0, c->st>>>(V, nb, v0, min(8, nv - v0), w, n, part, nv);
+  }
+  *nblocks = RED_BLOCKS;
+  return cudaGetLastError();
+}
+
+__global__ void k_arnoldi_coef_b(const double* part, int nblocks, int nv, z64* H, int j, int m, z64* coef, int first) {
+  __shared__ double sh[32];
+  const int v = blockIdx.x, r = blockIdx.y;
+  double re = 0, im = 0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const double* p = part + (((long long)r * nblocks + b) * nv + v) * 2;
+    re += p[0];
+    im += p[1];
+  }
+  const double tr = block_sum(re, sh);
+  const double ti = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    const z64 cv = mk<double>(tr, ti);
+    coef[(long long)r * (m + 1) + v] = cv;
+    z64* hc = H + (long long)r * (m + 1) * m + (long long)j * (m + 1);
+    hc[v] = first ? cv : hc[v] + cv;
+  }
+}
+
+cudaError_t launch_arnoldi_coef_b(ddm_ctx* c, const double* part, int nblocks, int nv, int nb, z64* H, int j, int m,
+                                  z64* coef, int first) {
+  ++c->nlaunch;
+  k_arnoldi_coef_b<<<dim3(nv, nb), 256, 0, c->st>>>(part, nblocks, nv, H, j, m, coef, first);
+  return cudaGetLastError();
+}
+
+__global__ void k_sub_axpy_b(const z64* V, int nb, int nv, const z64* coef, int m, z64* w, long long n) {
+  __shared__ z64 cs[128];
+  const int r = blockIdx.z;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) cs[v] = coef[(long long)r * (m + 1) + v];
+  __syncthreads();
+  z64* wr = w + (long long)r * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    z64 acc = wr[i];
+    for (int v = 0; v < nv; ++v) cfma(acc, -cs[v], V[((long long)v * nb + r) * n + i]);
+    wr[i] = acc;
+  }
+}
+
+cudaError_t launch_sub_axpy_b(ddm_ctx* c, const z64* V, int nb, int nv, const z64* coef, int m, z64* w, long long n) {
+  ++c->nlaunch;
+  k_sub_axpy_b<<<dim3(RED_BLOCKS * 2, 1, nb), 256, 0, c->st>>>(V, nb, nv, coef, m, w, n);
+  return cudaGetLastError();
+}
+
+// one thread per right-hand side: the Givens step of k_givens on its own H and gs
+__global__ void k_givens_b(int nb, int j, int m, const double* nrm2, z64* H, z64* gs, double* out_est) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  z64* Hr = H + (long long)r * (m + 1) * m;
+  z64* g = gs + (long long)r * (5 * m + 4);
+  z64* cs = g;
+  z64* sn = g + m;
+  z64* gg = g + 2 * m;
+  z64* col = Hr + (long long)j * (m + 1);
+  const double hn = sqrt(nrm2[r]);
+  col[j + 1] = mk<double>(hn, 0.0);
+  g[3 * m + 1] = mk<double>(hn > 0 ? 1.0 / hn : 0.0, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const z64 a = col[i], b = col[i + 1];
+    const z64 snc = mk<double>(sn[i].x, -sn[i].y);
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = cs[i] * b - snc * a;
+  }
+  const z64 a = col[j], b = col[j + 1];
+  const double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(b));
+  const double den = sqrt(aa * aa + bb * bb);
+  z64 cc, s;
+  if (den == 0.0) { cc = mk<double>(1, 0); s = mk<double>(0, 0); }
+  else if (aa == 0.0) { cc = mk<double>(0, 0); s = mk<double>(b.x / bb, -b.y / bb); }
+  else {
+    cc = mk<double>(aa / den, 0.0);
+    const z64 ph = mk<double>(a.x / aa, a.y / aa);
+    s = (1.0 / den) * (ph * mk<double>(b.x, -b.y));
+  }
+  cs[j] = cc;
+  sn[j] = s;
+  col[j] = cc * a + s * b;
+  col[j + 1] = mk<double>(0, 0);
+  const z64 gj = gg[j];
+  gg[j + 1] = -(mk<double>(s.x, -s.y) * gj);
+  gg[j] = cc * gj;
+  out_est[r] = sqrt(cabs2(gg[j + 1]));
+}
+
+cudaError_t launch_givens_b(ddm_ctx* c, int nb, int j, int m, const double* nrm2, z64* H, z64* gs, double* out_est) {
+  ++c->nlaunch;
+  k_givens_b<<<(nb + 63) / 64, 64, 0, c->st>>>(nb, j, m, nrm2, H, gs, out_est);
+  return cudaGetLastError();
+}
+
+// w_r *= gs_r[3m+1]
+__global__ void k_scale_b(z64* w, const z64* gs, int m, long long n) {
+  const int r = blockIdx.z;
+  const z64 s = gs[(long long)r * (5 * m + 4) + 3 * m + 1];
+  z64* wr = w + (long long)r * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    wr[i] = s * wr[i];
+}
+
+cudaError_t launch_scale_b(ddm_ctx* c, int nb, z64* w, const z64* gs, int m, long long n) {
+  ++c->nlaunch;
+  k_scale_b<<<dim3(1216, 1, nb), 256, 0, c->st>>>(w, gs, m, n);
+  return cudaGetLastError();
+}
+
+// dst_r = src_r * s[r]  (host-computed per right-hand side factors, in device memory)
+__global__ void k_scale_vec_b(const z64* src, const double* s, z64* dst, long long n) {
+  const int r = blockIdx.z;
+  const double sr = s[r];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[(long long)r * n + i] = sr * src[(long long)r * n + i];
+}
+
+cudaError_t launch_scale_vec_b(ddm_ctx* c, int nb, const z64* src, const double* s, z64* dst, long long n) {
+  ++c->nlaunch;
+  k_scale_vec_b<<<dim3(1216, 1, nb), 256, 0, c->st>>>(src, s, dst, n);
+  return cudaGetLastError();
+}
+
+// y_r = H_r(0:j_r, 0:j_r)^{-1} g_r(0:j_r), one thread per right-hand side
+__global__ void k_lsq_b(int nb, const int* jr, int m, const z64* H, z64* gs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  const int j = jr[r];
+  const z64* Hr = H + (long long)r * (m + 1) * m;
+  z64* g = gs + (long long)r * (5 * m + 4);
+  const z64* gg = g + 2 * m;
+  z64* y = g + 3 * m + 2;
+  for (int i = j - 1; i >= 0; --i) {
+    z64 acc = gg[i];
+    for (int k = i + 1; k < j; ++k) acc = acc - Hr[(long long)k * (m + 1) + i] * y[k];
+    y[i] = acc * cinv(Hr[(long long)i * (m + 1) + i]);
+  }
+}
+
+// x_r += Z_r(:, 0:j_r) y_r
+__global__ void k_update_x_b(int nb, const int* jr, int m, const z64* gs, const z64* Z, z64* x, long long n) {
+  __shared__ z64 ys[128];
+  const int r = blockIdx.z;
+  const int j = jr[r];
+  for (int v = threadIdx.x; v < j; v += blockDim.x) ys[v] = gs[(long long)r * (5 * m + 4) + 3 * m + 2 + v];
+  __syncthreads();
+  if (j == 0) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    z64 acc = x[(long long)r * n + i];
+    for (int v = 0; v < j; ++v) cfma(acc, ys[v], Z[((long long)v * nb + r) * n + i]);
+    x[(long long)r * n + i] = acc;
+  }
+}
+
+cudaError_t launch_lsq_update_b(ddm_ctx* c, int nb, const int* d_jr, int m, const z64* H, z64* gs, const z64* Z, z64* x,
+                                long long n) {
+  c->nlaunch += 2;
+  k_lsq_b<<<(nb + 63) / 64, 64, 0, c->st>>>(nb, d_jr, m, H, gs);
+  k_update_x_b<<<dim3(RED_BLOCKS * 2, 1, nb), 256, 0, c->st>>>(nb, d_jr, m, gs, Z, x, n);
+  return cudaGetLastError();
+}
+
+}  // namespace ddm

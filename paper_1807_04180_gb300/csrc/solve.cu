@@ -250,14 +250,18 @@ static cudaError_t solve_nr(ddm_ctx* c, const void* src, void* out, void* U, int
   const size_t el = sizeof(cplx<T>);
   const size_t fixed = (size_t)2 * NR * bpad * el + 16 + 2 * 32 * 8 + 16;
   const size_t stage = (size_t)SOLVE_RCH * maxld * el;
-  // as many pipeline stages as fit while every CTA of the grid is resident at once
   int dev = 0, nsm = 152, smem_sm = 228 * 1024, smem_blk = 227 * 1024;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // CTAs per SM: what the grid needs, capped by what registers allow
+  int reg_cap = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&reg_cap, k_solve2d<T, NR>, SOLVE_THREADS, 0);
   const long long ctas = (long long)c->g.nsub * ((nrhs + NR - 1) / NR);
-  const int per_sm = (int)std::min<long long>(4, std::max<long long>(1, (ctas + nsm - 1) / nsm));
+  int per_sm = (int)std::min<long long>(4, std::max<long long>(1, (ctas + nsm - 1) / nsm));
+  if (reg_cap > 0) per_sm = std::min(per_sm, reg_cap);
+  // as many pipeline stages as fit with per_sm CTAs resident
   size_t budget = std::min<size_t>((size_t)smem_blk, (size_t)smem_sm / per_sm - 1024);
   int nst = (int)std::min<size_t>(32, budget > fixed ? (budget - fixed) / stage : 0);
   nst = std::max(nst, 2);
@@ -272,11 +276,51 @@ static cudaError_t solve_nr(ddm_ctx* c, const void* src, void* out, void* U, int
 }
 
 template <typename T>
+static cudaError_t solve_with(ddm_ctx* c, int nr, const void* src, void* out, void* U, int nrhs) {
+  switch (nr) {
+    case 8: return solve_nr<T, 8>(c, src, out, U, nrhs);
+    case 4: return solve_nr<T, 4>(c, src, out, U, nrhs);
+    case 2: return solve_nr<T, 2>(c, src, out, U, nrhs);
+    default: return solve_nr<T, 1>(c, src, out, U, nrhs);
+  }
+}
+
+// Right-hand sides per CTA for nrhs right-hand sides: measured once per context and nrhs by
+// timing every candidate (1, 2, 4, 8; 8 only in complex64) on the call's own source into a
+// scratch output, then cached.  More right-hand sides per CTA read each factor block fewer
+// times but raise the registers per thread, which can cut the CTAs per SM.
+template <typename T>
 static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
-  if (nrhs >= 8 && sizeof(T) == 4) return solve_nr<T, 8>(c, src, out, U, nrhs);
-  if (nrhs >= 4) return solve_nr<T, 4>(c, src, out, U, nrhs);
-  if (nrhs >= 2) return solve_nr<T, 2>(c, src, out, U, nrhs);
-  return solve_nr<T, 1>(c, src, out, U, nrhs);
+  if (nrhs == 1) return solve_nr<T, 1>(c, src, out, U, 1);
+  auto it = c->tuned_nr.find(nrhs);
+  if (it == c->tuned_nr.end()) {
+    void* scratch = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, sizeof(cplx<T>) * c->g.ltotal * nrhs);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 1;
+    float best_ms = 1e30f;
+    for (int nr : {1, 2, 4, 8}) {
+      if (nr > nrhs || (nr == 8 && sizeof(T) != 4)) continue;
+      if ((e = solve_with<T>(c, nr, src, scratch, nullptr, nrhs)) != cudaSuccess) break;   // warm
+      cudaEventRecord(e0, c->st);
+      if ((e = solve_with<T>(c, nr, src, scratch, nullptr, nrhs)) != cudaSuccess) break;
+      cudaEventRecord(e1, c->st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->tune_log.push_back({nrhs, nr, ms});
+      if (ms < best_ms) { best_ms = ms; best = nr; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return e;
+    it = c->tuned_nr.emplace(nrhs, best).first;
+  }
+  return solve_with<T>(c, it->second, src, out, U, nrhs);
 }
 
 cudaError_t launch_local_solve(ddm_ctx* c, const void* src, void* out, void* accum, int nrhs) {

@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
                        ctypes.POINTER(ctypes.c_int64)],
         "ddm_factor_bytes": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
         "ddm_norms_noalloc": [_P, ctypes.c_int64, ctypes.c_int, _P, _P],
+        "ddm_autotune_log": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -275,6 +277,17 @@ def ddm_timing(ctx, enable: bool = True, reset: bool = False) -> dict:
     n = (ctypes.c_int64 * 6)()
     _check(lib().ddm_timing(ctx, int(bool(enable)), int(bool(reset)), ms, n), ctx)
     return {TIMING_SLOTS[i]: (ms[i], n[i]) for i in range(6)}
+
+
+def ddm_autotune_log(ctx):
+    """[(nrhs, right-hand sides per CTA, device ms)] measured by the local-solve autotuner."""
+    n = ctypes.c_int()
+    _check(lib().ddm_autotune_log(ctx, 0, None, None, None, ctypes.byref(n)), ctx)
+    a = (ctypes.c_int * max(n.value, 1))()
+    b = (ctypes.c_int * max(n.value, 1))()
+    m = (ctypes.c_float * max(n.value, 1))()
+    _check(lib().ddm_autotune_log(ctx, n.value, a, b, m, None), ctx)
+    return [(a[i], b[i], m[i]) for i in range(n.value)]
 
 
 def ddm_factor_bytes(ctx):

@@ -144,13 +144,18 @@ def uniform_cuts(n: int, parts: int) -> np.ndarray:
 
 
 def uneven_cuts(n: int, parts: int, seed: int, jitter: int) -> np.ndarray:
-    """Seeded uneven cuts: widths n/parts + U{-jitter..jitter}, the last width absorbing the rest."""
+    """Seeded uneven cuts: widths n/parts + U{-jitter..jitter}, then the sum corrected to n by
+    +-1 steps on randomly chosen parts, every width staying within n//parts - jitter ..
+    n//parts + jitter + 1."""
     rng = np.random.default_rng(seed)
     base = n // parts
     w = base + rng.integers(-jitter, jitter + 1, parts)
-    w[-1] = n - w[:-1].sum()
-    if w.min() < 1:
-        raise ValueError("jitter too large for this partition")
+    lo, hi = max(1, base - jitter), base + jitter + 1
+    while w.sum() != n:
+        step = 1 if w.sum() < n else -1
+        i = int(rng.integers(parts))
+        if lo <= w[i] + step <= hi:
+            w[i] += step
     return np.concatenate([[0], np.cumsum(w)]).astype(np.int64)
 
 

@@ -152,6 +152,13 @@ ddm_status ddm_solve(ddm_ctx *ctx, const void *f_dev, void *u_dev, int nrhs, dou
 ddm_status ddm_solve_host(ddm_ctx *ctx, const void *f_host, void *u_host, int nrhs, double tol, int max_it,
                           int mode, int K, int restart, ddm_info *info);
 
+/* Upper bound of the device bytes a context for `p` holds after ddm_setup,
+ * ddm_factor (every subdomain counted with its own factor) and an FGMRES
+ * solve of p->max_rhs right-hand sides with the given restart (0: no FGMRES
+ * workspace).  Pure arithmetic on the parameters: no CUDA call, usable for
+ * admission control before any allocation.  Errors: DDM_E_INVAL.            */
+ddm_status ddm_workspace_bytes(const ddm_params *p, int restart, int64_t *bytes);
+
 /* Release every device allocation of the context.  NULL is a no-op.        */
 ddm_status ddm_destroy(ddm_ctx *ctx);
 

@@ -837,6 +837,54 @@ extern "C" ddm_status ddm_timing(ddm_ctx* c, int enable, int reset, double* out_
   return DDM_OK;
 }
 
+extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int64_t* bytes) {
+  if (!p || !bytes) return fail(nullptr, DDM_E_INVAL, "null argument");
+  if ((p->dim != 2 && p->dim != 3) || p->overlap < 1 || p->pml < 1 || p->max_rhs < 1 || restart < 0)
+    return fail(nullptr, DDM_E_INVAL, "bad parameters");
+  const int d = p->dim, e = p->overlap + p->pml;
+  const long long el = p->precision == DDM_MIXED ? 8 : 16;
+  long long nglob = 1, ltotal = 1, nsub = 1, fac = 0, tab = 0;
+  std::vector<std::vector<long long>> widths(3);
+  for (int a = 0; a < d; ++a) {
+    if (p->n[a] < 1 || p->parts[a] < 1) return fail(nullptr, DDM_E_INVAL, "bad n / parts");
+    nglob *= p->n[a] + 2 * e;
+    nsub *= p->parts[a];
+    for (int i = 0; i < p->parts[a]; ++i) {
+      long long lo = p->cuts[a] ? p->cuts[a][i] : (p->n[a] * i) / p->parts[a];
+      long long hi = p->cuts[a] ? p->cuts[a][i + 1] : (p->n[a] * (i + 1)) / p->parts[a];
+      widths[a].push_back(hi - lo + 2 * e);
+      tab += 2 * (hi - lo + 2 * e) + 1;
+    }
+    tab += 2 * (p->n[a] + 2 * e) + 1;
+  }
+  // local length and factor storage (every subdomain distinct: the upper bound)
+  long long lsum = 0;
+  std::vector<long long> s1 = widths[0], s2 = d > 1 ? widths[1] : std::vector<long long>{1},
+                         s3 = d > 2 ? widths[2] : std::vector<long long>{1};
+  for (long long wz : s3)
+    for (long long wy : s2)
+      for (long long wx : s1) {
+        lsum += wx * wy * wz;
+        const long long b = d == 2 ? wx : wx * wy, m = d == 2 ? wy : wz, ldb = (b + 3) & ~3LL;
+        fac += m * b * ldb;
+      }
+  ltotal = lsum;
+  const long long R = p->max_rhs;
+  long long total = 0;
+  total += 8 * nglob;                           // k^2
+  total += el * ltotal * (2 * d + 1);           // local operator planes
+  total += 16 * nglob * (2 * d + 1);            // global operator planes
+  total += 16 * tab + 8 * ltotal;               // alpha tables, strip-node lists (upper bound)
+  total += el * ltotal * R * (3 + d);           // source, U and the ring of d step solutions
+  total += 16 * nglob * R * 3;                  // global work vectors
+  total += 8 * std::max<long long>(R * nsub * ((lsum / std::max(nsub, 1LL) + 127) / 128 + 1), R * 304LL * 2 * 122);
+  total += el * fac;                            // factors
+  if (restart > 0) total += 16 * nglob * R * (2LL * restart + 1);   // FGMRES V and Z
+  total += 64LL << 20;                          // descriptors, scalars, rounding
+  *bytes = total;
+  return DDM_OK;
+}
+
 extern "C" ddm_status ddm_autotune_log(const ddm_ctx* c, int cap, int* nrhs, int* nr, float* ms, int* count) {
   if (!c) return DDM_E_INVAL;
   const int n = (int)c->tune_log.size();

@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
                        ctypes.POINTER(ctypes.c_int64)],
         "ddm_factor_bytes": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
         "ddm_norms_noalloc": [_P, ctypes.c_int64, ctypes.c_int, _P, _P],
+        "ddm_workspace_bytes": [ctypes.POINTER(ddm_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
         "ddm_autotune_log": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)],
     }
@@ -169,6 +170,13 @@ def ddm_setup(params: ddm_params, omega: float, c_dev, stream=None):
     st = lib().ddm_setup(ctypes.byref(params), float(omega), _ptr(c_dev), _stream(stream), ctypes.byref(out))
     _check(st, None)
     return out
+
+
+def ddm_workspace_bytes(params: ddm_params, restart: int) -> int:
+    """Upper bound of a context's device bytes (set-up, factors, FGMRES workspace)."""
+    out = ctypes.c_int64()
+    _check(lib().ddm_workspace_bytes(ctypes.byref(params), int(restart), ctypes.byref(out)), None)
+    return out.value
 
 
 def ddm_set_medium(ctx, omega: float, c_dev) -> None:

@@ -51,3 +51,18 @@ def test_binding_refuses_cpu_tensors(built):
     from paper_1807_04180_gb300 import ddm
     with pytest.raises(TypeError):
         ddm._ptr(torch.zeros(4, dtype=torch.complex128))
+
+
+def test_workspace_estimate_is_pure_arithmetic_and_monotone(built):
+    """ddm_workspace_bytes needs no GPU; it grows with the grid, the right-hand sides and the
+    Krylov restart."""
+    from paper_1807_04180_gb300 import ddm, workloads as W
+    small = W.tiny_2d(n=24, parts=(2, 2))
+    big = W.tiny_2d(n=48, parts=(4, 4))
+    b = []
+    for wl, R, m in [(small, 1, 0), (small, 1, 20), (small, 4, 20), (big, 4, 20)]:
+        p, keep = ddm.params_from(wl, ddm.DDM_MIXED, R)
+        b.append(ddm.ddm_workspace_bytes(p, m))
+    assert b[0] < b[1] < b[2] < b[3]
+    p, keep = ddm.params_from(small, ddm.DDM_FP64, 1)
+    assert ddm.ddm_workspace_bytes(p, 0) > b[0]       # complex128 local storage

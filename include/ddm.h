@@ -152,6 +152,15 @@ ddm_status ddm_solve(ddm_ctx *ctx, const void *f_dev, void *u_dev, int nrhs, dou
 ddm_status ddm_solve_host(ddm_ctx *ctx, const void *f_host, void *u_host, int nrhs, double tol, int max_it,
                           int mode, int K, int restart, ddm_info *info);
 
+/* enable != 0: every preconditioner application M_K (ddm_apply, and inside
+ * ddm_solve's FGMRES) replays a CUDA graph of its kernels -- restriction, K
+ * batched local solves, K-1 transfers, assembly -- captured on the first use
+ * of each (nrhs, K) on a library-owned non-blocking stream and ordered with
+ * the context's stream by events.  Inputs and outputs pass through staging
+ * vectors held by the context.  0 turns it off.  2D partitions only.
+ * Errors: DDM_E_INVAL (3D).                                                  */
+ddm_status ddm_set_graph(ddm_ctx *ctx, int enable);
+
 /* Upper bound of the device bytes a context for `p` holds after ddm_setup,
  * ddm_factor (every subdomain counted with its own factor) and an FGMRES
  * solve of p->max_rhs right-hand sides with the given restart (0: no FGMRES
@@ -208,8 +217,10 @@ ddm_status ddm_steps(ddm_ctx *ctx, const void *b_dev, int nsteps, void *w_dev, v
 /* Device time of the kernels launched since the last reset, accumulated with
  * CUDA events on the context's stream when timing is enabled:
  * out_ms[0] local solves, [1] transfers, [2] assembly/restriction,
- * [3] global operator, [4] Krylov (Arnoldi, updates), [5] factorisation;
- * out_launches[i] the matching launch counts (either array may be NULL).
+ * [3] global operator, [4] Krylov (Arnoldi, updates), [5] factorisation,
+ * [6] graph replays of M_K (ddm_set_graph; their kernels are not in 0-2);
+ * out_launches[i] the matching launch counts (arrays of 7; either may be
+ * NULL).
  * enable != 0 turns recording on, 0 off; reset clears the sums.            */
 ddm_status ddm_timing(ddm_ctx *ctx, int enable, int reset, double *out_ms, int64_t *out_launches);
 

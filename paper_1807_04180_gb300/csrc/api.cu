@@ -298,6 +298,11 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
 extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (!c) return DDM_OK;
   if (c->st || true) cudaStreamSynchronize(c->st);
+  for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+  if (c->gstream) cudaStreamSynchronize(c->gstream), cudaStreamDestroy(c->gstream);
+  for (auto ev : c->gev) if (ev) cudaEventDestroy(ev);
+  if (c->d_gin) cudaFree(c->d_gin);
+  if (c->d_gout) cudaFree(c->d_gout);
   if (c->h_bscal) cudaFreeHost(c->h_bscal);
   if (c->d_bscal) cudaFree(c->d_bscal);
   if (c->d_jr) cudaFree(c->d_jr);
@@ -479,11 +484,72 @@ static ddm_status run_steps(ddm_ctx* c, const z64* b, int nrhs, int K, z64* w_ou
   return DDM_OK;
 }
 
+// M_K through a CUDA graph: the kernels of one application (restriction, K local solves,
+// K-1 transfers, assembly) are captured once per (nrhs, K) on a dedicated stream, reading and
+// writing fixed staging vectors, and replayed; the staging copies and the replay are ordered
+// after and before the context's stream with events.  The first call runs the application once
+// outside capture so that the local solve's autotuner has settled (it allocates and times).
+static ddm_status apply_graphed(ddm_ctx* c, const z64* src, z64* dst, int nrhs, int K) {
+  const long long n = c->g.nglob;
+  if (!c->gstream) {
+    CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
+    CK(cudaMalloc((void**)&c->d_gin, sizeof(z64) * n * c->p.max_rhs));
+    CK(cudaMalloc((void**)&c->d_gout, sizeof(z64) * n * c->p.max_rhs));
+  }
+  ddm_ctx::GraphRec* rec = nullptr;
+  for (auto& g : c->graphs) if (g.nrhs == nrhs && g.K == K) rec = &g;
+  CK(cudaMemcpyAsync(c->d_gin, src, sizeof(z64) * n * nrhs, cudaMemcpyDeviceToDevice, c->st));
+  if (!rec) {
+    CKS(run_steps(c, c->d_gin, nrhs, K, c->d_gout, nullptr, nullptr));   // settle the autotuner
+    CK(cudaStreamSynchronize(c->st));
+    const bool timing = c->timing;
+    c->timing = false;
+    cudaStream_t keep = c->st;
+    c->st = c->gstream;
+    const long long n0 = c->nlaunch;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+    ddm_status st = DDM_OK;
+    if (e == cudaSuccess) st = run_steps(c, c->d_gin, nrhs, K, c->d_gout, nullptr, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(c->gstream, &graph);
+    c->st = keep;
+    c->timing = timing;
+    if (e != cudaSuccess || e2 != cudaSuccess || st != DDM_OK)
+      return fail(c, DDM_E_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    cudaGraphDestroy(graph);
+    c->graphs.push_back({nrhs, K, exec, c->nlaunch - n0});
+    rec = &c->graphs.back();
+  }
+  CK(cudaEventRecord(c->gev[0], c->st));
+  CK(cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+  cudaError_t le;
+  {
+    cudaStream_t keep = c->st;
+    c->st = c->gstream;   // the timing scope records on the stream the graph runs on
+    {
+      TScope ts(c, T_GRAPH);
+      le = cudaGraphLaunch(rec->exec, c->gstream);
+    }
+    c->st = keep;
+  }
+  CK(le);
+  c->nlaunch += rec->kernels;
+  CK(cudaEventRecord(c->gev[1], c->gstream));
+  CK(cudaStreamWaitEvent(c->st, c->gev[1], 0));
+  CK(cudaMemcpyAsync(dst, c->d_gout, sizeof(z64) * n * nrhs, cudaMemcpyDeviceToDevice, c->st));
+  return DDM_OK;
+}
+
 extern "C" ddm_status ddm_apply(ddm_ctx* c, int K, const void* src_dev, void* dst_dev, int nrhs) {
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
   if (K < 1 || nrhs < 1 || nrhs > c->p.max_rhs || !src_dev || !dst_dev) return fail(c, DDM_E_INVAL, "bad K / nrhs / pointer");
   if (!c->factored) return fail(c, DDM_E_STATE, "ddm_factor must run before ddm_apply");
-  CKS(run_steps(c, (const z64*)src_dev, nrhs, K, (z64*)dst_dev, nullptr, nullptr));
+  if (c->use_graph) CKS(apply_graphed(c, (const z64*)src_dev, (z64*)dst_dev, nrhs, K));
+  else CKS(run_steps(c, (const z64*)src_dev, nrhs, K, (z64*)dst_dev, nullptr, nullptr));
   CK(cudaGetLastError());
   return DDM_OK;
 }
@@ -654,7 +720,10 @@ static ddm_status fgmres_batch(ddm_ctx* c, const z64* b, z64* x, int nb, double 
       z64* vj = V + (long long)j * nb * n;
       z64* zj = Z + (long long)j * nb * n;
       z64* w = V + (long long)(j + 1) * nb * n;
-      { ddm_status st = run_steps(c, vj, nb, K, zj, nullptr, nullptr); if (st != DDM_OK) { cleanup(); return st; } }
+      {
+        ddm_status st = c->use_graph ? apply_graphed(c, vj, zj, nb, K) : run_steps(c, vj, nb, K, zj, nullptr, nullptr);
+        if (st != DDM_OK) { cleanup(); return st; }
+      }
       steps += K;
       {
         TScope ts(c, T_GLOBAL);
@@ -834,6 +903,13 @@ extern "C" ddm_status ddm_timing(ddm_ctx* c, int enable, int reset, double* out_
   if (out_launches) for (int i = 0; i < T_NSLOT; ++i) out_launches[i] = c->t_n[i];
   if (reset) for (int i = 0; i < T_NSLOT; ++i) { c->t_ms[i] = 0; c->t_n[i] = 0; }
   c->timing = enable != 0;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_set_graph(ddm_ctx* c, int enable) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (enable && c->dim != 2) return fail(c, DDM_E_INVAL, "graph replay of M_K is implemented for 2D partitions");
+  c->use_graph = enable != 0;
   return DDM_OK;
 }
 

@@ -131,7 +131,7 @@ __device__ __forceinline__ Coef coef_at(const Geom& g, const int* tofs, const in
 // ---------------------------------------------------------------------------
 // timing slots (ddm_timing)
 // ---------------------------------------------------------------------------
-enum { T_SOLVE = 0, T_TRANSFER, T_ASSEMBLE, T_GLOBAL, T_KRYLOV, T_FACTOR, T_NSLOT };
+enum { T_SOLVE = 0, T_TRANSFER, T_ASSEMBLE, T_GLOBAL, T_KRYLOV, T_FACTOR, T_GRAPH, T_NSLOT };
 
 }  // namespace ddm
 
@@ -197,6 +197,14 @@ struct ddm_ctx {
   std::map<int, int> tuned_nr;
   struct TuneRec { int nrhs, nr; float ms; };
   std::vector<TuneRec> tune_log;
+  // CUDA graphs of one preconditioner application M_K, per (nrhs, K)
+  bool use_graph = false;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  ddm::z64* d_gin = nullptr;
+  ddm::z64* d_gout = nullptr;
+  struct GraphRec { int nrhs, K; cudaGraphExec_t exec; long long kernels; };
+  std::vector<GraphRec> graphs;
   // kernels launched by this context (ddm_kernel_launches)
   long long nlaunch = 0;
   // timing

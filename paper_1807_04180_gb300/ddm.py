@@ -28,7 +28,7 @@ DDM_FP64, DDM_MIXED = 0, 1
 DDM_STEPPING, DDM_FGMRES = 0, 1
 STATUS_NAMES = ["DDM_OK", "DDM_E_INVAL", "DDM_E_NOMEM", "DDM_E_CUDA", "DDM_E_STATE", "DDM_E_SINGULAR",
                 "DDM_E_NOCONV", "DDM_E_TIMEOUT", "DDM_E_BUDGET"]
-TIMING_SLOTS = ["solve", "transfer", "assemble", "global", "krylov", "factor"]
+TIMING_SLOTS = ["solve", "transfer", "assemble", "global", "krylov", "factor", "graph"]
 
 
 class ddm_params(ctypes.Structure):
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "ddm_factor_bytes": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
         "ddm_norms_noalloc": [_P, ctypes.c_int64, ctypes.c_int, _P, _P],
         "ddm_workspace_bytes": [ctypes.POINTER(ddm_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
+        "ddm_set_graph": [_P, ctypes.c_int],
         "ddm_autotune_log": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)],
     }
@@ -170,6 +171,10 @@ def ddm_setup(params: ddm_params, omega: float, c_dev, stream=None):
     st = lib().ddm_setup(ctypes.byref(params), float(omega), _ptr(c_dev), _stream(stream), ctypes.byref(out))
     _check(st, None)
     return out
+
+
+def ddm_set_graph(ctx, enable: bool = True) -> None:
+    _check(lib().ddm_set_graph(ctx, int(bool(enable))), ctx)
 
 
 def ddm_workspace_bytes(params: ddm_params, restart: int) -> int:
@@ -281,10 +286,10 @@ def ddm_steps(ctx, b_dev, nsteps: int, w_dev=None, u_last_dev=None, want_res: bo
 
 
 def ddm_timing(ctx, enable: bool = True, reset: bool = False) -> dict:
-    ms = (ctypes.c_double * 6)()
-    n = (ctypes.c_int64 * 6)()
+    ms = (ctypes.c_double * 7)()
+    n = (ctypes.c_int64 * 7)()
     _check(lib().ddm_timing(ctx, int(bool(enable)), int(bool(reset)), ms, n), ctx)
-    return {TIMING_SLOTS[i]: (ms[i], n[i]) for i in range(6)}
+    return {TIMING_SLOTS[i]: (ms[i], n[i]) for i in range(7)}
 
 
 def ddm_autotune_log(ctx):

@@ -100,6 +100,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+# ----------------------------------------------------------------------------------- ranks
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The maximum of a per-rank float over all ranks (identity on one rank): the timed region
+    of every replica is reported as its slowest rank's."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -158,10 +171,7 @@ def run_ours(args, rank, world, local_rank):
     elapsed_ms = max(dev_ms, wall * 1e3)
     tms = D.ddm_timing(ctx, enable=False)
     launches = D.ddm_kernel_launches(ctx)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
     ms_per_step = elapsed_ms / args.steps
     # dominant kernel: the batched local solves (k_solve2d)
     solve_ms, solve_n = tms["solve"]
@@ -217,10 +227,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     out["e2e"] = {"value": world * 1e3 / e2e_ms, "unit": UNIT,
                   "h2d_bytes_per_step": int(c_h.numel() * 8 + f_h.numel() * 16),
                   "d2h_bytes_per_step": int(u_h.numel() * 16)}

@@ -161,6 +161,17 @@ ddm_status ddm_solve_host(ddm_ctx *ctx, const void *f_host, void *u_host, int nr
  * Errors: DDM_E_INVAL (3D).                                                  */
 ddm_status ddm_set_graph(ddm_ctx *ctx, int enable);
 
+/* Block solves of Algorithm 3.1 on the tensor cores (DDM_MIXED only).  In 3D
+ * every plane step of the forward and backward sweeps is a complex
+ * contraction G_k Y over all subdomains and right-hand sides sharing a factor
+ * (Section 3, the block LDU solve); with enable != 0 (the default) it runs
+ * on tcgen05 in split TF32 ("3xTF32": hi*hi + hi*lo + lo*hi, FP32
+ * accumulation, FP32-level accuracy), from a packed copy of the factor that
+ * ddm_factor writes; 0 selects the CUDA-core FP32 kernels.  DDM_FP64 contexts
+ * always use FP64 CUDA cores.  Takes effect from the next solve.
+ * Errors: DDM_E_INVAL (null context).                                       */
+ddm_status ddm_set_tensor_cores(ddm_ctx *ctx, int enable);
+
 /* Upper bound of the device bytes a context for `p` holds after ddm_setup,
  * ddm_factor (every subdomain counted with its own factor) and an FGMRES
  * solve of p->max_rhs right-hand sides with the given restart (0: no FGMRES

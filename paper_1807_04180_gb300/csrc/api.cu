@@ -308,7 +308,8 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (c->d_jr) cudaFree(c->d_jr);
   void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_sidx, c->d_smask, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
-                  c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs};
+                  c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs,
+                  c->d_gtc, c->d_ytc};
   for (void* q : ptrs) if (q) cudaFree(q);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -422,7 +423,10 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   {
     TScope ts(c, T_FACTOR);
     if (c->dim == 2) CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
-    else CK(launch_factor3d(c, reps));
+    else {
+      CK(launch_factor3d(c, reps));
+      if (c->prec == DDM_MIXED) CK(tc3d_pack_factors(c));
+    }
   }
   cudaEventRecord(e1, c->st);
   CK(cudaStreamSynchronize(c->st));
@@ -913,6 +917,12 @@ extern "C" ddm_status ddm_set_graph(ddm_ctx* c, int enable) {
   return DDM_OK;
 }
 
+extern "C" ddm_status ddm_set_tensor_cores(ddm_ctx* c, int enable) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  c->use_tc = enable != 0;
+  return DDM_OK;
+}
+
 extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int64_t* bytes) {
   if (!p || !bytes) return fail(nullptr, DDM_E_INVAL, "null argument");
   if ((p->dim != 2 && p->dim != 3) || p->overlap < 1 || p->pml < 1 || p->max_rhs < 1 || restart < 0)
@@ -934,7 +944,7 @@ extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int6
     tab += 2 * (p->n[a] + 2 * e) + 1;
   }
   // local length and factor storage (every subdomain distinct: the upper bound)
-  long long lsum = 0;
+  long long lsum = 0, tcfac = 0, tcy = 0;
   std::vector<long long> s1 = widths[0], s2 = d > 1 ? widths[1] : std::vector<long long>{1},
                          s3 = d > 2 ? widths[2] : std::vector<long long>{1};
   for (long long wz : s3)
@@ -943,6 +953,10 @@ extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int6
         lsum += wx * wy * wz;
         const long long b = d == 2 ? wx : wx * wy, m = d == 2 ? wy : wz, ldb = (b + 3) & ~3LL;
         fac += m * b * ldb;
+        if (d == 3 && p->precision == DDM_MIXED) {
+          tcfac += 4 * tc3d_packed_floats((int)b, (int)m);
+          tcy = std::max(tcy, 4 * tc3d_packed_floats((int)b, 1) / std::max(1LL, (b + 127) / 128));
+        }
       }
   ltotal = lsum;
   const long long R = p->max_rhs;
@@ -955,6 +969,7 @@ extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int6
   total += 16 * nglob * R * 3;                  // global work vectors
   total += 8 * std::max<long long>(R * nsub * ((lsum / std::max(nsub, 1LL) + 127) / 128 + 1), R * 304LL * 2 * 122);
   total += el * fac;                            // factors
+  total += tcfac + tcy * ((nsub * R + 127) / 128);   // 3D tensor-core packs (factors, one operand)
   if (restart > 0) total += 16 * nglob * R * (2LL * restart + 1);   // FGMRES V and Z
   total += 64LL << 20;                          // descriptors, scalars, rounding
   *bytes = total;

@@ -11,6 +11,7 @@
 // (a GEMM per plane, right-hand sides as columns) with the Schur coupling fused into the
 // operand load and the t / x / U updates fused into the epilogue.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "ddm_internal.cuh"
@@ -277,6 +278,15 @@ static cudaError_t solve3d_t(ddm_ctx* c, const void* src, void* out, void* U, in
     const int b = c->fac_b[f], m = c->fac_m[f], ldb = c->fac_ldb[f];
     const long long len = (long long)b * m;
     const cplx<T>* lc = (const cplx<T>*)c->d_lcoef + s.vofs * 7;
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->use_tc && c->d_gtc) {
+        if ((e = tc3d_sweeps(c, f, c->d_col3d, ncol, lc + 5 * len, lc + 6 * len, (const c32*)src, (c32*)out,
+                             (c32*)U)) != cudaSuccess)
+          return e;
+        if (f + 1 < c->nfac) cudaStreamSynchronize(c->st);
+        continue;
+      }
+    }
     dim3 grid((b + G3_BM - 1) / G3_BM, (ncol + G3_BN - 1) / G3_BN);
     for (int i = 0; i < 2 * m - 1; ++i) {
       const int pass = i < m ? 0 : 1;

@@ -193,6 +193,13 @@ struct ddm_ctx {
   // 3D solves: column offsets of the right-hand sides sharing a factor
   long long* d_col3d = nullptr;
   size_t col3d_cap = 0;
+  // tensor-core (tcgen05) path of the mixed-precision 3D plane steps: packed 3xTF32 factors and
+  // the packed operand of the current plane step
+  bool use_tc = true;
+  float* d_gtc = nullptr;
+  std::vector<long long> tc_ofs;
+  float* d_ytc = nullptr;
+  size_t ytc_cap = 0;
   // autotuned right-hand sides per CTA of the 2D local solve, per nrhs, and the timings taken
   std::map<int, int> tuned_nr;
   struct TuneRec { int nrhs, nr; float ms; };
@@ -254,4 +261,8 @@ cudaError_t launch_lsq_update_b(ddm_ctx* c, int nb, const int* d_jr, int m, cons
 int ring_slots(const ddm_ctx* c);
 cudaError_t launch_factor3d(ddm_ctx* c, const std::vector<int>& reps);
 cudaError_t launch_local_solve3d(ddm_ctx* c, const void* src, void* out, void* U, int nrhs);
+long long tc3d_packed_floats(int b, int m);
+cudaError_t tc3d_pack_factors(ddm_ctx* c);
+cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, const c32* cS, const c32* cN,
+                        const c32* src, c32* out, c32* U);
 }  // namespace ddm

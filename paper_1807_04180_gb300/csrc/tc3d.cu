@@ -1,0 +1,275 @@
+// Tensor-core (tcgen05) plane step of the 3D local solves in mixed precision.
+//
+// A 3D subdomain factor keeps, per z-plane k, the dense block G_k = D_k^{-1} (b x b complex,
+// b = ext_x * ext_y); every subdomain and right-hand side that shares the factor is a column of
+// one operand Y, so each plane step of the forward and backward sweeps is the complex
+// contraction C = G_k Y (the block solves of Algorithm 3.1 in 3D).  Here it runs on the
+// 5th-generation tensor cores as four real products per complex product (planar real and
+// imaginary parts, the minus sign through the instruction's negate-B bit), each in "3xTF32":
+// every FP32 operand x is split into hi = tf32(x) and lo = x - hi, and hi*hi + hi*lo + lo*hi is
+// accumulated in FP32 in tensor memory, which keeps FP32-level accuracy.
+//
+// Data layout (all K-major, no swizzle, see tcgen05.cuh):
+//  - factor, packed once after the factorisation: per plane k, i-tile (128 rows of G_k) and
+//    K-chunk (8 columns j) one 16 KB block of four 4 KB planes {Re hi, Re lo, Im hi, Im lo};
+//  - operand Y, packed before each plane step: per q-tile (128 columns) and K-chunk the same
+//    four planes of Y^T (row q = column q of Y).
+// One CTA computes the 128 x 128 output tile D[q][i] = sum_j Y[j][q] G_k[i][j] for one q-tile and
+// one i-tile: a producer thread streams the (factor, operand) block pairs through a ring of
+// shared-memory stages with cp.async.bulk, one thread issues the 12 MMAs per chunk and frees the
+// stage with tcgen05.commit, and after the last chunk the four warps read the two accumulators
+// (real: TMEM columns 0-127, imaginary: 128-255) back with tcgen05.ld and apply the sweep's
+// update to the local vectors (the same update as the CUDA-core plane step).
+#include <algorithm>
+#include <vector>
+
+#include "ddm_internal.cuh"
+#include "tcgen05.cuh"
+
+namespace ddm {
+
+constexpr int TC3_TILE = 128;                  // rows of an i-tile, columns of a q-tile
+constexpr int TC3_KC = 8;                      // K (j) per chunk = one tf32 MMA step
+constexpr int TC3_PLANE = TC3_TILE * TC3_KC;   // floats per plane of a block (4 KB)
+constexpr int TC3_BLOCK = 4 * TC3_PLANE;       // floats per block (16 KB)
+constexpr int TC3_NST = 6;                     // ring stages, 32 KB each
+constexpr int TC3_SMEM = TC3_NST * 2 * TC3_BLOCK * 4 + 1024;
+
+// packed factor of one plane: blocks (it, kc), it < nIT, kc < nKC
+__global__ void k_g3_pack(const c32* __restrict__ G, long long fofs, int ldb, int b, int m, int nIT, int nKC,
+                          float* __restrict__ gtc) {
+  const long long nI = (long long)nIT * TC3_TILE, nJ = (long long)nKC * TC3_KC;
+  const long long total = (long long)m * nJ * nI;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % nI);
+    const long long r = idx / nI;
+    const int j = (int)(r % nJ);
+    const int k = (int)(r / nJ);
+    c32 v = mk<float>(0.f, 0.f);
+    if (i < b && j < b) v = G[fofs + ((long long)k * b + j) * ldb + i];
+    float rh, rl, ih, il;
+    tc::split_tf32(v.x, rh, rl);
+    tc::split_tf32(v.y, ih, il);
+    const int it = i / TC3_TILE, kc = j / TC3_KC;
+    float* blk = gtc + (((long long)k * nIT + it) * nKC + kc) * TC3_BLOCK;
+    const int e = tc::kmajor_index(i % TC3_TILE, j % TC3_KC, TC3_KC);
+    blk[e] = rh;
+    blk[TC3_PLANE + e] = rl;
+    blk[2 * TC3_PLANE + e] = ih;
+    blk[3 * TC3_PLANE + e] = il;
+  }
+}
+
+// operand of plane step (pass, k) for the columns q < ncol (zero padding elsewhere):
+//   pass 0: Y[j][q] = src_q[k b + j] - c_zm(j, k) out_q[(k-1) b + j]
+//   pass 1: Y[j][q] = c_zp(j, k) out_q[(k+1) b + j]
+__global__ void k_y3_pack(int pass, int k, int b, int nKC, int nQT, const long long* __restrict__ colofs, int ncol,
+                          const c32* __restrict__ src, const c32* __restrict__ out, const c32* __restrict__ cS,
+                          const c32* __restrict__ cN, float* __restrict__ ytc) {
+  const long long nJ = (long long)nKC * TC3_KC;
+  const long long total = (long long)nQT * TC3_TILE * nJ;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % nJ);
+    const int q = (int)(idx / nJ);
+    c32 v = mk<float>(0.f, 0.f);
+    if (q < ncol && j < b) {
+      const long long base = colofs[q];
+      if (pass == 0) {
+        v = src[base + (long long)k * b + j];
+        if (k > 0) v = v - cS[(long long)k * b + j] * out[base + (long long)(k - 1) * b + j];
+      } else {
+        v = cN[(long long)k * b + j] * out[base + (long long)(k + 1) * b + j];
+      }
+    }
+    float rh, rl, ih, il;
+    tc::split_tf32(v.x, rh, rl);
+    tc::split_tf32(v.y, ih, il);
+    const int qt = q / TC3_TILE, kc = j / TC3_KC;
+    float* blk = ytc + ((long long)qt * nKC + kc) * TC3_BLOCK;
+    const int e = tc::kmajor_index(q % TC3_TILE, j % TC3_KC, TC3_KC);
+    blk[e] = rh;
+    blk[TC3_PLANE + e] = rl;
+    blk[2 * TC3_PLANE + e] = ih;
+    blk[3 * TC3_PLANE + e] = il;
+  }
+}
+
+// plane step on the tensor cores; grid (nIT, nQT), 128 threads
+__global__ void __launch_bounds__(128, 1)
+    k_gemm3d_tc(const float* __restrict__ gplane, const float* __restrict__ ytc, int nKC, int b, int pass, int k, int m,
+                const long long* __restrict__ colofs, int ncol, c32* out, c32* U, int* err) {
+  extern __shared__ unsigned char dsm_raw[];
+  __shared__ __align__(8) uint64_t s_full[TC3_NST], s_empty[TC3_NST], s_accf;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int it = blockIdx.x, qt = blockIdx.y;
+  // stages: 1 KB aligned (16 bytes is what the copies and descriptors need)
+  const uint32_t dsm = (tc::smem_addr(dsm_raw) + 1023u) & ~1023u;
+  const uint32_t STAGE_BYTES = 2 * TC3_BLOCK * 4;
+
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), 256);
+  if (tid == 0) {
+    for (int s = 0; s < TC3_NST; ++s) {
+      tc::bar_init(tc::smem_addr(&s_full[s]), 1);
+      tc::bar_init(tc::smem_addr(&s_empty[s]), 1);
+    }
+    tc::bar_init(tc::smem_addr(&s_accf), 1);
+    s_fail = 0;
+    tc::bar_init_fence();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = s_tmem;
+
+  const float* gbase = gplane + (long long)it * nKC * TC3_BLOCK;
+  const float* ybase = ytc + (long long)qt * nKC * TC3_BLOCK;
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kc = 0; kc < nKC; ++kc) {
+      const int s = kc % TC3_NST;
+      if (kc >= TC3_NST && !tc::bar_wait(tc::smem_addr(&s_empty[s]), (uint32_t)((kc / TC3_NST) - 1) & 1u)) {
+        s_fail = 1;
+        atomicOr(err, ERRBIT_TIMEOUT);
+        break;
+      }
+      const uint32_t fb = tc::smem_addr(&s_full[s]);
+      const uint32_t st = dsm + (uint32_t)s * STAGE_BYTES;
+      tc::bar_expect_tx(fb, STAGE_BYTES);
+      tc::bulk_load(st, gbase + (long long)kc * TC3_BLOCK, TC3_BLOCK * 4, fb);
+      tc::bulk_load(st + TC3_BLOCK * 4, ybase + (long long)kc * TC3_BLOCK, TC3_BLOCK * 4, fb);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: A = Y^T tile (M = 128 columns q), B = G_k tile (N = 128 rows i), K = 8 per chunk
+    constexpr uint32_t ID = tc::idesc_tf32(TC3_TILE, TC3_TILE, false);
+    constexpr uint32_t IDN = tc::idesc_tf32(TC3_TILE, TC3_TILE, true);
+    const uint32_t accR = tmem, accI = tmem + TC3_TILE;
+    const uint32_t LBO = 128, SBO = (TC3_KC / 4) * 128;
+    for (int kc = 0; kc < nKC; ++kc) {
+      const int s = kc % TC3_NST;
+      if (!tc::bar_wait(tc::smem_addr(&s_full[s]), (uint32_t)(kc / TC3_NST) & 1u)) {
+        s_fail = 1;
+        atomicOr(err, ERRBIT_TIMEOUT);
+        break;
+      }
+      tc::fence_after();
+      const uint32_t g0 = dsm + (uint32_t)s * STAGE_BYTES, y0 = g0 + TC3_BLOCK * 4;
+      const uint64_t Grh = tc::sdesc(g0, LBO, SBO), Grl = tc::sdesc(g0 + TC3_PLANE * 4, LBO, SBO);
+      const uint64_t Gih = tc::sdesc(g0 + 2 * TC3_PLANE * 4, LBO, SBO), Gil = tc::sdesc(g0 + 3 * TC3_PLANE * 4, LBO, SBO);
+      const uint64_t Yrh = tc::sdesc(y0, LBO, SBO), Yrl = tc::sdesc(y0 + TC3_PLANE * 4, LBO, SBO);
+      const uint64_t Yih = tc::sdesc(y0 + 2 * TC3_PLANE * 4, LBO, SBO), Yil = tc::sdesc(y0 + 3 * TC3_PLANE * 4, LBO, SBO);
+      const uint32_t first = kc > 0 ? 1u : 0u;
+      // Re: Yr Gr - Yi Gi
+      tc::mma_tf32(accR, Yrh, Grh, ID, first);
+      tc::mma_tf32(accR, Yrh, Grl, ID, 1u);
+      tc::mma_tf32(accR, Yrl, Grh, ID, 1u);
+      tc::mma_tf32(accR, Yih, Gih, IDN, 1u);
+      tc::mma_tf32(accR, Yih, Gil, IDN, 1u);
+      tc::mma_tf32(accR, Yil, Gih, IDN, 1u);
+      // Im: Yr Gi + Yi Gr
+      tc::mma_tf32(accI, Yrh, Gih, ID, first);
+      tc::mma_tf32(accI, Yrh, Gil, ID, 1u);
+      tc::mma_tf32(accI, Yrl, Gih, ID, 1u);
+      tc::mma_tf32(accI, Yih, Grh, ID, 1u);
+      tc::mma_tf32(accI, Yih, Grl, ID, 1u);
+      tc::mma_tf32(accI, Yil, Grh, ID, 1u);
+      tc::mma_commit(tc::smem_addr(&s_empty[s]));
+    }
+    tc::mma_commit(tc::smem_addr(&s_accf));
+  }
+  __syncwarp();
+  const bool got = tc::bar_wait(tc::smem_addr(&s_accf), 0u);
+  const int bad = __syncthreads_or(!got || s_fail);
+  tc::fence_after();
+  if (!bad) {
+    const int q = qt * TC3_TILE + warp * 32 + lane;
+    const long long base = q < ncol ? colofs[q] + (long long)k * b : 0;
+    const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < TC3_TILE; c0 += 16) {
+      float vr[16], vi[16];
+      tc::tmem_ld16(lanebase + (uint32_t)c0, vr);
+      tc::tmem_ld16(lanebase + (uint32_t)(TC3_TILE + c0), vi);
+      if (q < ncol) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int i = it * TC3_TILE + c0 + jj;
+          if (i < b) {
+            const long long o = base + i;
+            c32 v = mk<float>(vr[jj], vi[jj]);
+            if (pass == 1) v = out[o] - v;
+            out[o] = v;
+            if (U && (pass == 1 || k == m - 1)) U[o] = U[o] + v;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, ERRBIT_TIMEOUT);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
+// ------------------------------------------------------------------------------------ host
+long long tc3d_packed_floats(int b, int m) {
+  const long long nIT = (b + TC3_TILE - 1) / TC3_TILE, nKC = (b + TC3_KC - 1) / TC3_KC;
+  return (long long)m * nIT * nKC * TC3_BLOCK;
+}
+
+// pack every factor after the factorisation (mixed precision only)
+cudaError_t tc3d_pack_factors(ddm_ctx* c) {
+  cudaError_t e = cudaSuccess;
+  long long total = 0;
+  c->tc_ofs.assign(c->nfac, 0);
+  for (int f = 0; f < c->nfac; ++f) {
+    c->tc_ofs[f] = total;
+    total += tc3d_packed_floats(c->fac_b[f], c->fac_m[f]);
+  }
+  if (c->d_gtc) { cudaFree(c->d_gtc); c->d_gtc = nullptr; }
+  if ((e = cudaMalloc((void**)&c->d_gtc, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
+  for (int f = 0; f < c->nfac; ++f) {
+    const int b = c->fac_b[f], m = c->fac_m[f];
+    const int nIT = (b + TC3_TILE - 1) / TC3_TILE, nKC = (b + TC3_KC - 1) / TC3_KC;
+    ++c->nlaunch;
+    k_g3_pack<<<1216, 256, 0, c->st>>>((const c32*)c->d_G, c->fac_ofs[f], c->fac_ldb[f], b, m, nIT, nKC,
+                                       c->d_gtc + c->tc_ofs[f]);
+  }
+  return cudaGetLastError();
+}
+
+// all plane steps of the forward and backward sweeps of one factor group
+cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, const c32* cS, const c32* cN,
+                        const c32* src, c32* out, c32* U) {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
+  if (e != cudaSuccess) return e;
+  const int b = c->fac_b[f], m = c->fac_m[f];
+  const int nIT = (b + TC3_TILE - 1) / TC3_TILE, nKC = (b + TC3_KC - 1) / TC3_KC;
+  const int nQT = (ncol + TC3_TILE - 1) / TC3_TILE;
+  const size_t need = (size_t)nQT * nKC * TC3_BLOCK;
+  if (need > c->ytc_cap) {
+    if (c->d_ytc) cudaFree(c->d_ytc);
+    c->d_ytc = nullptr;
+    c->ytc_cap = 0;
+    if ((e = cudaMalloc((void**)&c->d_ytc, sizeof(float) * need)) != cudaSuccess) return e;
+    c->ytc_cap = need;
+  }
+  const long long plane = (long long)nIT * nKC * TC3_BLOCK;
+  const float* gtc = c->d_gtc + c->tc_ofs[f];
+  const long long packed = (long long)nQT * TC3_TILE * nKC * TC3_KC;
+  const int pgrid = (int)std::min<long long>((packed + 255) / 256, 152LL * 16);
+  for (int s = 0; s < 2 * m - 1; ++s) {
+    const int pass = s < m ? 0 : 1;
+    const int k = pass == 0 ? s : 2 * m - 2 - s;
+    c->nlaunch += 2;
+    k_y3_pack<<<pgrid, 256, 0, c->st>>>(pass, k, b, nKC, nQT, d_colofs, ncol, src, out, cS, cN, c->d_ytc);
+    k_gemm3d_tc<<<dim3(nIT, nQT), 128, TC3_SMEM, c->st>>>(gtc + k * plane, c->d_ytc, nKC, b, pass, k, m, d_colofs,
+                                                          ncol, out, U, c->d_err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ddm

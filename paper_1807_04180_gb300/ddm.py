@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
         "ddm_norms_noalloc": [_P, ctypes.c_int64, ctypes.c_int, _P, _P],
         "ddm_workspace_bytes": [ctypes.POINTER(ddm_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
         "ddm_set_graph": [_P, ctypes.c_int],
+        "ddm_set_tensor_cores": [_P, ctypes.c_int],
         "ddm_autotune_log": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)],
     }
@@ -175,6 +176,10 @@ def ddm_setup(params: ddm_params, omega: float, c_dev, stream=None):
 
 def ddm_set_graph(ctx, enable: bool = True) -> None:
     _check(lib().ddm_set_graph(ctx, int(bool(enable))), ctx)
+
+
+def ddm_set_tensor_cores(ctx, enable: bool = True) -> None:
+    _check(lib().ddm_set_tensor_cores(ctx, int(bool(enable))), ctx)
 
 
 def ddm_workspace_bytes(params: ddm_params, restart: int) -> int:

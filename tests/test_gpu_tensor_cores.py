@@ -1,0 +1,81 @@
+"""Tensor-core (tcgen05, split TF32) block solves against the FP64 oracle and against the
+CUDA-core FP32 kernels, on cases that span several 128-row tiles of the factor blocks and
+several 128-column tiles of the right-hand-side operand, each with a ragged tail."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import from_local, oracle_of, rel, to_local  # noqa: E402
+from paper_1807_04180_gb300 import ddm as D  # noqa: E402
+from paper_1807_04180_gb300 import workloads as W  # noqa: E402
+
+
+def cplx(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _uneven(wl, cuts):
+    wl.cuts = tuple(np.array(c) for c in cuts)
+    return wl
+
+
+def cases3d():
+    return {
+        # b = 20 x 20 = 400 rows per plane block: 4 row tiles, the last 16 rows; 8 x 17 = 136 columns
+        "gauss-b400": (W.tiny_3d(seed=11, n=24, parts=(2, 2, 2), ov=1, npml=3), 17),
+        # uneven parts (plane blocks of 19x22, 23x20, ... rows), ov = 2
+        "uneven-ov2": (_uneven(W.tiny_3d(seed=12, n=22, parts=(2, 2, 2), ov=2, npml=3),
+                               ([0, 9, 22], [0, 12, 22], [0, 10, 22])), 3),
+        # constant medium: one shared factor, all 8 x 20 columns in one contraction
+        "const-shared": (W.tiny_3d(seed=13, n=20, parts=(2, 2, 2), ov=1, npml=3, medium="const"), 20),
+    }
+
+
+CASES3D = cases3d()
+
+
+def _local_solves(wl, nrhs, tc):
+    o = oracle_of(wl)
+    s = D.Solver(wl, precision=D.DDM_MIXED, max_rhs=nrhs).factor()
+    D.ddm_set_tensor_cores(s.ctx, tc)
+    rng = np.random.default_rng(5)
+    srcs = [{R: cplx(rng, o.sub_shape[R]) for R in o.subs} for _ in range(nrhs)]
+    src = np.concatenate([to_local(o, sr, np.complex64) for sr in srcs])
+    u = torch.zeros(src.shape, dtype=torch.complex64, device="cuda")
+    D.ddm_local_solve(s.ctx, s.to_dev(src), u, nrhs)
+    out = u.cpu().numpy().reshape(nrhs, -1)
+    s.close()
+    return o, srcs, out
+
+
+@pytest.mark.parametrize("name", list(CASES3D))
+def test_3d_tensor_core_local_solves_match_oracle(name):
+    wl, nrhs = CASES3D[name]
+    o, srcs, tc = _local_solves(wl, nrhs, True)
+    _, _, cc = _local_solves(wl, nrhs, False)
+    err_tc = err_cc = 0.0
+    for r in range(nrhs):
+        got_tc, got_cc = from_local(o, tc[r]), from_local(o, cc[r])
+        for R in o.subs:
+            if r < 3 or R == o.subs[-1]:          # the oracle's sparse solves: a sample of them
+                ref = o.local_solve(R, srcs[r][R])
+                err_tc = max(err_tc, rel(got_tc[R], ref))
+                err_cc = max(err_cc, rel(got_cc[R], ref))
+    # FP32-level accuracy: the bound of the FP32 local solves, and no worse than the CUDA-core
+    # FP32 kernels on the same inputs (split TF32 carries about 21 bits against FP32's 24)
+    assert err_tc < 2e-4, (err_tc, err_cc)
+    assert err_tc < 4 * err_cc + 1e-6, (err_tc, err_cc)
+
+
+def test_3d_tensor_core_fgmres_reaches_1e6():
+    wl, _ = CASES3D["gauss-b400"]
+    o = oracle_of(wl)
+    s = D.Solver(wl, precision=D.DDM_MIXED).factor()
+    u = torch.zeros(o.gshape, dtype=torch.complex128, device="cuda")
+    info = D.ddm_solve(s.ctx, s.to_dev(wl.f[0]), u, tol=1e-6, max_it=300, mode=D.DDM_FGMRES, K=4, restart=40)
+    b = o.rhs(wl.f[0])
+    x = u.cpu().numpy()
+    assert info["converged"] and np.linalg.norm(b - o.apply_global(x)) / np.linalg.norm(b) <= 1e-6
+    s.close()

@@ -309,7 +309,7 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_sidx, c->d_smask, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
                   c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs,
-                  c->d_gtc, c->d_ytc};
+                  c->d_gtc, c->d_ytc, c->d_tcpart};
   for (void* q : ptrs) if (q) cudaFree(q);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }

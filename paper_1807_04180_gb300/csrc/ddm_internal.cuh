@@ -200,6 +200,8 @@ struct ddm_ctx {
   std::vector<long long> tc_ofs;
   float* d_ytc = nullptr;
   size_t ytc_cap = 0;
+  float* d_tcpart = nullptr;     // split-K partial tiles of the current plane step
+  size_t tcpart_cap = 0;
   // autotuned right-hand sides per CTA of the 2D local solve, per nrhs, and the timings taken
   std::map<int, int> tuned_nr;
   struct TuneRec { int nrhs, nr; float ms; };

@@ -26,6 +26,7 @@
 #include "ddm_internal.cuh"
 #include "tcgen05.cuh"
 
+
 namespace ddm {
 
 constexpr int TC3_TILE = 128;                  // rows of an i-tile, columns of a q-tile
@@ -96,16 +97,22 @@ __global__ void k_y3_pack(int pass, int k, int b, int nKC, int nQT, const long l
   }
 }
 
-// plane step on the tensor cores; grid (nIT, nQT), 128 threads
+// Contraction of one plane step (pass, k) on the tensor cores; grid (nIT, nQT, nsplit), 128
+// threads.  Warp 0 lane 0 streams the (factor, operand) block pairs of this CTA's K range (the
+// range is split nsplit ways across blockIdx.z so that the grid fills the SMs) through the stage
+// ring, warp 1 lane 0 issues the MMAs, and the four warps then store the FP32 accumulators as
+// the partial tile part[tile][split][q][0..127 real | 128..255 imaginary] (coalesced 16-byte
+// stores).  k_epi3d adds the partials and applies the sweep's update.
 __global__ void __launch_bounds__(128, 1)
-    k_gemm3d_tc(const float* __restrict__ gplane, const float* __restrict__ ytc, int nKC, int b, int pass, int k, int m,
-                const long long* __restrict__ colofs, int ncol, c32* out, c32* U, int* err) {
+    k_gemm3d_tc(const float* __restrict__ gplane, const float* __restrict__ ycur, int nKC, int nsplit,
+                float* __restrict__ part, int* err) {
   extern __shared__ unsigned char dsm_raw[];
   __shared__ __align__(8) uint64_t s_full[TC3_NST], s_empty[TC3_NST], s_accf;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int it = blockIdx.x, qt = blockIdx.y;
+  const int it = blockIdx.x, qt = blockIdx.y, split = blockIdx.z;
+  const int kc0 = (int)((long long)split * nKC / nsplit), kc1 = (int)((long long)(split + 1) * nKC / nsplit);
   // stages: 1 KB aligned (16 bytes is what the copies and descriptors need)
   const uint32_t dsm = (tc::smem_addr(dsm_raw) + 1023u) & ~1023u;
   const uint32_t STAGE_BYTES = 2 * TC3_BLOCK * 4;
@@ -126,12 +133,12 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = s_tmem;
 
   const float* gbase = gplane + (long long)it * nKC * TC3_BLOCK;
-  const float* ybase = ytc + (long long)qt * nKC * TC3_BLOCK;
+  const float* ybase = ycur + (long long)qt * nKC * TC3_BLOCK;
   if (warp == 0 && lane == 0) {
     // producer
-    for (int kc = 0; kc < nKC; ++kc) {
-      const int s = kc % TC3_NST;
-      if (kc >= TC3_NST && !tc::bar_wait(tc::smem_addr(&s_empty[s]), (uint32_t)((kc / TC3_NST) - 1) & 1u)) {
+    for (int kc = kc0; kc < kc1; ++kc) {
+      const int u = kc - kc0, s = u % TC3_NST;
+      if (u >= TC3_NST && !tc::bar_wait(tc::smem_addr(&s_empty[s]), (uint32_t)((u / TC3_NST) - 1) & 1u)) {
         s_fail = 1;
         atomicOr(err, ERRBIT_TIMEOUT);
         break;
@@ -148,9 +155,9 @@ __global__ void __launch_bounds__(128, 1)
     constexpr uint32_t IDN = tc::idesc_tf32(TC3_TILE, TC3_TILE, true);
     const uint32_t accR = tmem, accI = tmem + TC3_TILE;
     const uint32_t LBO = 128, SBO = (TC3_KC / 4) * 128;
-    for (int kc = 0; kc < nKC; ++kc) {
-      const int s = kc % TC3_NST;
-      if (!tc::bar_wait(tc::smem_addr(&s_full[s]), (uint32_t)(kc / TC3_NST) & 1u)) {
+    for (int kc = kc0; kc < kc1; ++kc) {
+      const int u = kc - kc0, s = u % TC3_NST;
+      if (!tc::bar_wait(tc::smem_addr(&s_full[s]), (uint32_t)(u / TC3_NST) & 1u)) {
         s_fail = 1;
         atomicOr(err, ERRBIT_TIMEOUT);
         break;
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(128, 1)
       const uint64_t Gih = tc::sdesc(g0 + 2 * TC3_PLANE * 4, LBO, SBO), Gil = tc::sdesc(g0 + 3 * TC3_PLANE * 4, LBO, SBO);
       const uint64_t Yrh = tc::sdesc(y0, LBO, SBO), Yrl = tc::sdesc(y0 + TC3_PLANE * 4, LBO, SBO);
       const uint64_t Yih = tc::sdesc(y0 + 2 * TC3_PLANE * 4, LBO, SBO), Yil = tc::sdesc(y0 + 3 * TC3_PLANE * 4, LBO, SBO);
-      const uint32_t first = kc > 0 ? 1u : 0u;
+      const uint32_t first = kc > kc0 ? 1u : 0u;
       // Re: Yr Gr - Yi Gi
       tc::mma_tf32(accR, Yrh, Grh, ID, first);
       tc::mma_tf32(accR, Yrh, Grl, ID, 1u);
@@ -185,26 +192,15 @@ __global__ void __launch_bounds__(128, 1)
   const int bad = __syncthreads_or(!got || s_fail);
   tc::fence_after();
   if (!bad) {
-    const int q = qt * TC3_TILE + warp * 32 + lane;
-    const long long base = q < ncol ? colofs[q] + (long long)k * b : 0;
+    const int q = warp * 32 + lane;
+    const long long tile = (long long)qt * gridDim.x + it;
+    float4* dst = reinterpret_cast<float4*>(part + ((tile * nsplit + split) * TC3_TILE + q) * (2 * TC3_TILE));
     const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < TC3_TILE; c0 += 16) {
-      float vr[16], vi[16];
-      tc::tmem_ld16(lanebase + (uint32_t)c0, vr);
-      tc::tmem_ld16(lanebase + (uint32_t)(TC3_TILE + c0), vi);
-      if (q < ncol) {
+    for (int c0 = 0; c0 < 2 * TC3_TILE; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(lanebase + (uint32_t)c0, v);
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int i = it * TC3_TILE + c0 + jj;
-          if (i < b) {
-            const long long o = base + i;
-            c32 v = mk<float>(vr[jj], vi[jj]);
-            if (pass == 1) v = out[o] - v;
-            out[o] = v;
-            if (U && (pass == 1 || k == m - 1)) U[o] = U[o] + v;
-          }
-        }
-      }
+      for (int j = 0; j < 4; ++j) __stcg(dst + c0 / 4 + j, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
     }
   } else if (tid == 0) {
     atomicOr(err, ERRBIT_TIMEOUT);
@@ -212,6 +208,61 @@ __global__ void __launch_bounds__(128, 1)
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
+// Epilogue of plane step (pass, k): one thread per (tile, q, i), consecutive threads along i.
+// C = sum of the nsplit partials (in split order), then the sweep's update
+//   pass 0: out = C (at k = m-1 also U += C);  pass 1: x = out - C, out = x, U += x,
+// and, when a next step (npass, nk) exists, its operand packed into ynext from the same values:
+//   npass 0 (nk = k+1): Y[j][q] = src_q[nk b + j] - c_zm(j, nk) C[j][q]
+//   npass 1 (nk = k-1, or m-2 at the turn): Y[j][q] = c_zp(j, nk) out_q[(nk+1) b + j]
+// (coefn = the c_zm or c_zp plane nk; rows b <= j < 8 nKC of the operand are written as zeros).
+__global__ void __launch_bounds__(256) k_epi3d(const float* __restrict__ part, int nIT, int nQT, int nsplit, int nKC,
+                                               int b, int pass, int k, int m, int npass, int nk,
+                                               const c32* __restrict__ coefn, const long long* __restrict__ colofs,
+                                               int ncol, const c32* __restrict__ src, c32* out, c32* U,
+                                               float* __restrict__ ynext) {
+  const long long total = (long long)nIT * nQT * TC3_TILE * TC3_TILE;
+  const int jpad = nKC * TC3_KC;
+  const bool upd = U && (pass == 1 || k == m - 1);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int il = (int)(idx % TC3_TILE);
+    const long long r = idx / TC3_TILE;
+    const int ql = (int)(r % TC3_TILE);
+    const long long tile = r / TC3_TILE;
+    const int it = (int)(tile % nIT), qt = (int)(tile / nIT);
+    const int q = qt * TC3_TILE + ql, i = it * TC3_TILE + il;
+    if (q >= ncol || i >= jpad) continue;
+    c32 v = mk<float>(0.f, 0.f);
+    const long long base = colofs[q];
+    if (i < b) {
+      const float* p = part + (tile * nsplit * TC3_TILE + ql) * (2 * TC3_TILE) + il;
+      float vr = 0.f, vi = 0.f;
+      for (int sp = 0; sp < nsplit; ++sp) {
+        vr += __ldcg(p + (long long)sp * TC3_TILE * (2 * TC3_TILE));
+        vi += __ldcg(p + (long long)sp * TC3_TILE * (2 * TC3_TILE) + TC3_TILE);
+      }
+      v = mk<float>(vr, vi);
+      const long long o = base + (long long)k * b + i;
+      if (pass == 1) v = out[o] - v;
+      out[o] = v;
+      if (upd) U[o] = U[o] + v;
+    }
+    if (npass >= 0) {
+      c32 y = mk<float>(0.f, 0.f);
+      if (i < b) y = npass == 0 ? src[base + (long long)nk * b + i] - coefn[i] * v : coefn[i] * v;
+      float rh, rl, ih, il2;
+      tc::split_tf32(y.x, rh, rl);
+      tc::split_tf32(y.y, ih, il2);
+      float* blk = ynext + ((long long)qt * nKC + i / TC3_KC) * TC3_BLOCK;
+      const int e = tc::kmajor_index(ql, i % TC3_KC, TC3_KC);
+      blk[e] = rh;
+      blk[TC3_PLANE + e] = rl;
+      blk[2 * TC3_PLANE + e] = ih;
+      blk[3 * TC3_PLANE + e] = il2;
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------ host
@@ -249,25 +300,52 @@ cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, 
   const int b = c->fac_b[f], m = c->fac_m[f];
   const int nIT = (b + TC3_TILE - 1) / TC3_TILE, nKC = (b + TC3_KC - 1) / TC3_KC;
   const int nQT = (ncol + TC3_TILE - 1) / TC3_TILE;
-  const size_t need = (size_t)nQT * nKC * TC3_BLOCK;
+  const size_t need = (size_t)nQT * nKC * TC3_BLOCK;   // one operand buffer; two are kept
   if (need > c->ytc_cap) {
     if (c->d_ytc) cudaFree(c->d_ytc);
     c->d_ytc = nullptr;
     c->ytc_cap = 0;
-    if ((e = cudaMalloc((void**)&c->d_ytc, sizeof(float) * need)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&c->d_ytc, sizeof(float) * 2 * need)) != cudaSuccess) return e;
+    // padding rows (columns q >= ncol) stay zero in both buffers
+    if ((e = cudaMemsetAsync(c->d_ytc, 0, sizeof(float) * 2 * need, c->st)) != cudaSuccess) return e;
     c->ytc_cap = need;
   }
+  // split K so that tiles x splits fill the SMs once (one CTA per SM: 197 KB of stages)
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = nIT * nQT;
+  const int nsplit = std::max(1, std::min({8, nKC, std::max(nsm, 1) / tiles}));
+  const size_t pneed = (size_t)tiles * nsplit * TC3_TILE * 2 * TC3_TILE;
+  if (pneed > c->tcpart_cap) {
+    if (c->d_tcpart) cudaFree(c->d_tcpart);
+    c->d_tcpart = nullptr;
+    c->tcpart_cap = 0;
+    if ((e = cudaMalloc((void**)&c->d_tcpart, sizeof(float) * pneed)) != cudaSuccess) return e;
+    c->tcpart_cap = pneed;
+  }
+  const long long etotal = (long long)tiles * TC3_TILE * TC3_TILE;
+  const int egrid = (int)std::min<long long>((etotal + 255) / 256, 152LL * 64);
   const long long plane = (long long)nIT * nKC * TC3_BLOCK;
   const float* gtc = c->d_gtc + c->tc_ofs[f];
   const long long packed = (long long)nQT * TC3_TILE * nKC * TC3_KC;
   const int pgrid = (int)std::min<long long>((packed + 255) / 256, 152LL * 16);
+  float* ybuf[2] = {c->d_ytc, c->d_ytc + need};
+  ++c->nlaunch;
+  k_y3_pack<<<pgrid, 256, 0, c->st>>>(0, 0, b, nKC, nQT, d_colofs, ncol, src, out, cS, cN, ybuf[0]);
   for (int s = 0; s < 2 * m - 1; ++s) {
     const int pass = s < m ? 0 : 1;
     const int k = pass == 0 ? s : 2 * m - 2 - s;
+    // the step after this one: forward k+1, the turn to backward m-2, backward k-1, or none
+    const int sn = s + 1;
+    const int npass = sn >= 2 * m - 1 ? -1 : (sn < m ? 0 : 1);
+    const int nk = npass < 0 ? 0 : (npass == 0 ? sn : 2 * m - 2 - sn);
+    const c32* coefn = npass == 0 ? cS + (long long)nk * b : cN + (long long)nk * b;
     c->nlaunch += 2;
-    k_y3_pack<<<pgrid, 256, 0, c->st>>>(pass, k, b, nKC, nQT, d_colofs, ncol, src, out, cS, cN, c->d_ytc);
-    k_gemm3d_tc<<<dim3(nIT, nQT), 128, TC3_SMEM, c->st>>>(gtc + k * plane, c->d_ytc, nKC, b, pass, k, m, d_colofs,
-                                                          ncol, out, U, c->d_err);
+    k_gemm3d_tc<<<dim3(nIT, nQT, nsplit), 128, TC3_SMEM, c->st>>>(gtc + k * plane, ybuf[s & 1], nKC, nsplit,
+                                                                  c->d_tcpart, c->d_err);
+    k_epi3d<<<egrid, 256, 0, c->st>>>(c->d_tcpart, nIT, nQT, nsplit, nKC, b, pass, k, m, npass, nk, coefn, d_colofs,
+                                      ncol, src, out, U, ybuf[(s + 1) & 1]);
   }
   return cudaGetLastError();
 }

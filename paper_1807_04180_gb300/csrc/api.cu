@@ -309,7 +309,7 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_sidx, c->d_smask, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
                   c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs,
-                  c->d_gtc, c->d_ytc, c->d_tcpart};
+                  c->d_gtc, c->d_ytc, c->d_tcpart, c->d_gtc2, c->d_tc2ofs};
   for (void* q : ptrs) if (q) cudaFree(q);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -422,7 +422,10 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   cudaEventRecord(e0, c->st);
   {
     TScope ts(c, T_FACTOR);
-    if (c->dim == 2) CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
+    if (c->dim == 2) {
+      CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
+      if (c->prec == DDM_MIXED && c->p.max_rhs >= 16) CK(tc2d_pack_factors(c));
+    }
     else {
       CK(launch_factor3d(c, reps));
       if (c->prec == DDM_MIXED) CK(tc3d_pack_factors(c));
@@ -923,6 +926,19 @@ extern "C" ddm_status ddm_set_tensor_cores(ddm_ctx* c, int enable) {
   return DDM_OK;
 }
 
+extern "C" ddm_status ddm_set_rhs_per_cta(ddm_ctx* c, int nr) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (nr != 0 && nr != 1 && nr != 2 && nr != 4 && nr != 8 && nr != 16 && nr != 32 && nr != 64)
+    return fail(c, DDM_E_INVAL, "right-hand sides per CTA must be 0 (autotuned), 1, 2, 4, 8, 16, 32 or 64");
+  if (nr == 8 && c->prec != DDM_MIXED) return fail(c, DDM_E_INVAL, "8 right-hand sides per CTA need DDM_MIXED");
+  if (nr >= 16 && (c->dim != 2 || c->prec != DDM_MIXED || !c->d_gtc2 || !tc2d_supported(c, nr)))
+    return fail(c, DDM_E_INVAL,
+                "16-64 right-hand sides per CTA run on the tensor cores: 2D, DDM_MIXED, max_rhs >= 16, factored, "
+                "and the operand must fit in shared memory");
+  c->forced_nr = nr;
+  return DDM_OK;
+}
+
 extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int64_t* bytes) {
   if (!p || !bytes) return fail(nullptr, DDM_E_INVAL, "null argument");
   if ((p->dim != 2 && p->dim != 3) || p->overlap < 1 || p->pml < 1 || p->max_rhs < 1 || restart < 0)
@@ -953,6 +969,7 @@ extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int6
         lsum += wx * wy * wz;
         const long long b = d == 2 ? wx : wx * wy, m = d == 2 ? wy : wz, ldb = (b + 3) & ~3LL;
         fac += m * b * ldb;
+        if (d == 2 && p->precision == DDM_MIXED && p->max_rhs >= 16) tcfac += 4 * tc2d_packed_floats((int)b, (int)m);
         if (d == 3 && p->precision == DDM_MIXED) {
           tcfac += 4 * tc3d_packed_floats((int)b, (int)m);
           tcy = std::max(tcy, 4 * tc3d_packed_floats((int)b, 1) / std::max(1LL, (b + 127) / 128));

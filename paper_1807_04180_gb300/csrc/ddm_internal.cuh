@@ -202,8 +202,14 @@ struct ddm_ctx {
   size_t ytc_cap = 0;
   float* d_tcpart = nullptr;     // split-K partial tiles of the current plane step
   size_t tcpart_cap = 0;
+  // tensor-core path of the mixed-precision 2D multi-right-hand-side solves: packed 3xTF32
+  // factors (written by ddm_factor when max_rhs >= 16) and their per-factor offsets
+  float* d_gtc2 = nullptr;
+  long long* d_tc2ofs = nullptr;
+  std::vector<long long> tc2_ofs;
   // autotuned right-hand sides per CTA of the 2D local solve, per nrhs, and the timings taken
   std::map<int, int> tuned_nr;
+  int forced_nr = 0;             // ddm_set_rhs_per_cta: 0 = autotuned
   struct TuneRec { int nrhs, nr; float ms; };
   std::vector<TuneRec> tune_log;
   // CUDA graphs of one preconditioner application M_K, per (nrhs, K)
@@ -264,6 +270,10 @@ int ring_slots(const ddm_ctx* c);
 cudaError_t launch_factor3d(ddm_ctx* c, const std::vector<int>& reps);
 cudaError_t launch_local_solve3d(ddm_ctx* c, const void* src, void* out, void* U, int nrhs);
 long long tc3d_packed_floats(int b, int m);
+long long tc2d_packed_floats(int b, int m);
+cudaError_t tc2d_pack_factors(ddm_ctx* c);
+bool tc2d_supported(const ddm_ctx* c, int nrt);
+cudaError_t tc2d_solve(ddm_ctx* c, int nrt, const void* src, void* out, void* U, int nrhs);
 cudaError_t tc3d_pack_factors(ddm_ctx* c);
 cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, const c32* cS, const c32* cN,
                         const c32* src, c32* out, c32* U);

@@ -275,8 +275,11 @@ static cudaError_t solve_nr(ddm_ctx* c, const void* src, void* out, void* U, int
   return cudaGetLastError();
 }
 
+// nr <= 8: CUDA-core kernel with nr right-hand sides per CTA; nr = 16, 32, 64: tensor-core kernel
+// (complex64 with a packed factor only) with nr right-hand sides per CTA
 template <typename T>
 static cudaError_t solve_with(ddm_ctx* c, int nr, const void* src, void* out, void* U, int nrhs) {
+  if (nr >= 16) return tc2d_solve(c, nr, src, out, U, nrhs);
   switch (nr) {
     case 8: return solve_nr<T, 8>(c, src, out, U, nrhs);
     case 4: return solve_nr<T, 4>(c, src, out, U, nrhs);
@@ -285,14 +288,18 @@ static cudaError_t solve_with(ddm_ctx* c, int nr, const void* src, void* out, vo
   }
 }
 
-// Right-hand sides per CTA for nrhs right-hand sides: measured once per context and nrhs by
-// timing every candidate (1, 2, 4, 8; 8 only in complex64) on the call's own source into a
-// scratch output, then cached.  More right-hand sides per CTA read each factor block fewer
-// times but raise the registers per thread, which can cut the CTAs per SM.
+// Kernel and right-hand sides per CTA for nrhs right-hand sides: measured once per context and
+// nrhs by timing every candidate on the call's own source into a scratch output, then cached.
+// CUDA-core candidates: 1, 2, 4, 8 (8 only in complex64) right-hand sides per CTA -- more read
+// each factor block fewer times but raise the registers per thread, which can cut the CTAs per
+// SM.  Tensor-core candidates (complex64, packed factor, tensor cores enabled): 16, 32, 64 per CTA.
 template <typename T>
 static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
   if (nrhs == 1) return solve_nr<T, 1>(c, src, out, U, 1);
-  auto it = c->tuned_nr.find(nrhs);
+  const bool tc = sizeof(T) == 4 && c->use_tc && c->d_gtc2;
+  if (c->forced_nr > 0 && (c->forced_nr < 16 || tc)) return solve_with<T>(c, c->forced_nr, src, out, U, nrhs);
+  const int key = tc ? nrhs : -nrhs;   // cached choices with and without the tensor cores
+  auto it = c->tuned_nr.find(key);
   if (it == c->tuned_nr.end()) {
     void* scratch = nullptr;
     cudaError_t e = cudaMalloc(&scratch, sizeof(cplx<T>) * c->g.ltotal * nrhs);
@@ -302,8 +309,10 @@ static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int 
     cudaEventCreate(&e1);
     int best = 1;
     float best_ms = 1e30f;
-    for (int nr : {1, 2, 4, 8}) {
-      if (nr > nrhs || (nr == 8 && sizeof(T) != 4)) continue;
+    for (int nr : {1, 2, 4, 8, 16, 32, 64}) {
+      if (nr == 8 && sizeof(T) != 4) continue;
+      if (nr <= 8 && nr > nrhs) continue;
+      if (nr >= 16 && (!tc || nr / 2 > nrhs || !tc2d_supported(c, nr))) continue;
       if ((e = solve_with<T>(c, nr, src, scratch, nullptr, nrhs)) != cudaSuccess) break;   // warm
       cudaEventRecord(e0, c->st);
       if ((e = solve_with<T>(c, nr, src, scratch, nullptr, nrhs)) != cudaSuccess) break;
@@ -318,7 +327,7 @@ static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int 
     cudaEventDestroy(e1);
     cudaFree(scratch);
     if (e != cudaSuccess) return e;
-    it = c->tuned_nr.emplace(nrhs, best).first;
+    it = c->tuned_nr.emplace(key, best).first;
   }
   return solve_with<T>(c, it->second, src, out, U, nrhs);
 }

@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "ddm_workspace_bytes": [ctypes.POINTER(ddm_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
         "ddm_set_graph": [_P, ctypes.c_int],
         "ddm_set_tensor_cores": [_P, ctypes.c_int],
+        "ddm_set_rhs_per_cta": [_P, ctypes.c_int],
         "ddm_autotune_log": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)],
     }
@@ -180,6 +181,10 @@ def ddm_set_graph(ctx, enable: bool = True) -> None:
 
 def ddm_set_tensor_cores(ctx, enable: bool = True) -> None:
     _check(lib().ddm_set_tensor_cores(ctx, int(bool(enable))), ctx)
+
+
+def ddm_set_rhs_per_cta(ctx, nr: int = 0) -> None:
+    _check(lib().ddm_set_rhs_per_cta(ctx, int(nr)), ctx)
 
 
 def ddm_workspace_bytes(params: ddm_params, restart: int) -> int:

@@ -174,11 +174,11 @@ ddm_status ddm_set_tensor_cores(ddm_ctx *ctx, int enable);
 
 /* Kernel choice of the 2D local solves (Algorithm 3.1's block solves) for
  * nrhs > 1: nr = 1, 2, 4, 8 right-hand sides per CTA on the CUDA cores
- * (8: DDM_MIXED only), or nr = 16, 32, 64 per CTA on the tensor cores
- * (DDM_MIXED contexts with max_rhs >= 16, after ddm_factor, which then keeps
- * a packed split-TF32 copy of the factors; the right-hand-side operand of a
- * CTA must fit in shared memory).  0 (the default) picks the fastest
- * candidate by timing each once per context and nrhs (ddm_autotune_log).
+ * (8: DDM_MIXED only), or nr = 64 per CTA on the tensor cores (DDM_MIXED
+ * contexts with max_rhs >= 16, after ddm_factor, which then keeps a packed
+ * split-TF32 copy of the factors; blocks of at most 128 rows).  0 (the
+ * default) picks the fastest candidate by timing each once per context and
+ * nrhs (ddm_autotune_log; the tensor-core candidate from nrhs >= 8).
  * Errors: DDM_E_INVAL (value not listed, or the tensor-core conditions not
  * met).                                                                     */
 ddm_status ddm_set_rhs_per_cta(ddm_ctx *ctx, int nr);

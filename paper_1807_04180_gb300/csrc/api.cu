@@ -928,13 +928,13 @@ extern "C" ddm_status ddm_set_tensor_cores(ddm_ctx* c, int enable) {
 
 extern "C" ddm_status ddm_set_rhs_per_cta(ddm_ctx* c, int nr) {
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
-  if (nr != 0 && nr != 1 && nr != 2 && nr != 4 && nr != 8 && nr != 16 && nr != 32 && nr != 64)
-    return fail(c, DDM_E_INVAL, "right-hand sides per CTA must be 0 (autotuned), 1, 2, 4, 8, 16, 32 or 64");
+  if (nr != 0 && nr != 1 && nr != 2 && nr != 4 && nr != 8 && nr != 64)
+    return fail(c, DDM_E_INVAL, "right-hand sides per CTA must be 0 (autotuned), 1, 2, 4, 8 or 64");
   if (nr == 8 && c->prec != DDM_MIXED) return fail(c, DDM_E_INVAL, "8 right-hand sides per CTA need DDM_MIXED");
-  if (nr >= 16 && (c->dim != 2 || c->prec != DDM_MIXED || !c->d_gtc2 || !tc2d_supported(c, nr)))
+  if (nr == 64 && (c->dim != 2 || c->prec != DDM_MIXED || !c->d_gtc2 || !tc2d_supported(c, nr)))
     return fail(c, DDM_E_INVAL,
-                "16-64 right-hand sides per CTA run on the tensor cores: 2D, DDM_MIXED, max_rhs >= 16, factored, "
-                "and the operand must fit in shared memory");
+                "64 right-hand sides per CTA run on the tensor cores: 2D, DDM_MIXED, max_rhs >= 16, factored, "
+                "blocks of at most 128 rows whose operand and two ring stages fit in shared memory");
   c->forced_nr = nr;
   return DDM_OK;
 }

@@ -275,11 +275,11 @@ static cudaError_t solve_nr(ddm_ctx* c, const void* src, void* out, void* U, int
   return cudaGetLastError();
 }
 
-// nr <= 8: CUDA-core kernel with nr right-hand sides per CTA; nr = 16, 32, 64: tensor-core kernel
-// (complex64 with a packed factor only) with nr right-hand sides per CTA
+// nr <= 8: CUDA-core kernel with nr right-hand sides per CTA; nr = 64: tensor-core kernel
+// (complex64 with a packed factor only), 64 right-hand sides per CTA
 template <typename T>
 static cudaError_t solve_with(ddm_ctx* c, int nr, const void* src, void* out, void* U, int nrhs) {
-  if (nr >= 16) return tc2d_solve(c, nr, src, out, U, nrhs);
+  if (nr > 8) return tc2d_solve(c, nr, src, out, U, nrhs);
   switch (nr) {
     case 8: return solve_nr<T, 8>(c, src, out, U, nrhs);
     case 4: return solve_nr<T, 4>(c, src, out, U, nrhs);
@@ -292,30 +292,34 @@ static cudaError_t solve_with(ddm_ctx* c, int nr, const void* src, void* out, vo
 // nrhs by timing every candidate on the call's own source into a scratch output, then cached.
 // CUDA-core candidates: 1, 2, 4, 8 (8 only in complex64) right-hand sides per CTA -- more read
 // each factor block fewer times but raise the registers per thread, which can cut the CTAs per
-// SM.  Tensor-core candidates (complex64, packed factor, tensor cores enabled): 16, 32, 64 per CTA.
+// SM.  Tensor-core candidate (complex64, packed factor, tensor cores enabled, nrhs >= 8): 64 per CTA.
 template <typename T>
 static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
   if (nrhs == 1) return solve_nr<T, 1>(c, src, out, U, 1);
   const bool tc = sizeof(T) == 4 && c->use_tc && c->d_gtc2;
-  if (c->forced_nr > 0 && (c->forced_nr < 16 || tc)) return solve_with<T>(c, c->forced_nr, src, out, U, nrhs);
+  if (c->forced_nr > 0 && (c->forced_nr <= 8 || tc)) return solve_with<T>(c, c->forced_nr, src, out, U, nrhs);
   const int key = tc ? nrhs : -nrhs;   // cached choices with and without the tensor cores
   auto it = c->tuned_nr.find(key);
   if (it == c->tuned_nr.end()) {
+    // scratch output and accumulator: the candidates are timed with the accumulation the DDM
+    // steps ask for
     void* scratch = nullptr;
-    cudaError_t e = cudaMalloc(&scratch, sizeof(cplx<T>) * c->g.ltotal * nrhs);
+    cudaError_t e = cudaMalloc(&scratch, 2 * sizeof(cplx<T>) * c->g.ltotal * nrhs);
     if (e != cudaSuccess) return e;
+    void* uscratch = (char*)scratch + sizeof(cplx<T>) * c->g.ltotal * nrhs;
+    cudaMemsetAsync(uscratch, 0, sizeof(cplx<T>) * c->g.ltotal * nrhs, c->st);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int best = 1;
     float best_ms = 1e30f;
-    for (int nr : {1, 2, 4, 8, 16, 32, 64}) {
+    for (int nr : {1, 2, 4, 8, 64}) {
       if (nr == 8 && sizeof(T) != 4) continue;
       if (nr <= 8 && nr > nrhs) continue;
-      if (nr >= 16 && (!tc || nr / 2 > nrhs || !tc2d_supported(c, nr))) continue;
-      if ((e = solve_with<T>(c, nr, src, scratch, nullptr, nrhs)) != cudaSuccess) break;   // warm
+      if (nr > 8 && (!tc || nrhs < 8 || !tc2d_supported(c, nr))) continue;
+      if ((e = solve_with<T>(c, nr, src, scratch, uscratch, nrhs)) != cudaSuccess) break;   // warm
       cudaEventRecord(e0, c->st);
-      if ((e = solve_with<T>(c, nr, src, scratch, nullptr, nrhs)) != cudaSuccess) break;
+      if ((e = solve_with<T>(c, nr, src, scratch, uscratch, nrhs)) != cudaSuccess) break;
       cudaEventRecord(e1, c->st);
       cudaEventSynchronize(e1);
       float ms = 0.f;

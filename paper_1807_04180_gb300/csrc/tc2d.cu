@@ -3,19 +3,29 @@
 // The block solves of Algorithm 3.1 in 2D (x-lines as blocks, G_k = D_k^{-1} from factor.cu):
 //   forward   y_k = r_k - c_S(., k) t_{k-1},  t_k = G_k y_k            (k = 0..m-1)
 //   backward  x_{m-1} = t_{m-1},  x_k = t_k - G_k (c_N(., k) x_{k+1})   (k = m-2..0)
-// With NRT right-hand sides per CTA every block step is a complex contraction of the b x b block
-// G_k with a b x NRT operand, here on the 5th-generation tensor cores in split TF32 ("3xTF32",
-// FP32 accumulation in tensor memory, FP32-level accuracy).  One CTA per (subdomain, group of NRT
-// right-hand sides; the groups of a subdomain adjacent in launch order) runs the whole sweep:
+// With 64 right-hand sides per CTA every block step is a complex contraction of the b x b block
+// G_k with a b x 64 operand, done here on the 5th-generation tensor cores in split TF32
+// ("3xTF32": x = hi + lo with hi = tf32(x); hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor
+// memory, FP32-level accuracy) as ONE real product per split term:
+//   A (M = 128 rows): row 2r + a is the real (a = 0) or imaginary (a = 1) part of right-hand
+//     side r's block vector, K = the b columns j;
+//   B (N = 2 bp rows, bp = b rounded up to 8): rows [Re G_k ; Im G_k], K = j;
+//   D = A B^T in tensor memory: D[2r+a][c bp + i] = sum_j Y_a(r, j) G_c(i, j),
+// so that Re(G y) = D[2r][i] - D[2r+1][bp+i] and Im(G y) = D[2r][bp+i] + D[2r+1][i].  N = 2 bp
+// (up to 256) keeps every MMA at the full tensor rate (measured: an M=128 x N x K=8 tf32 MMA takes
+// N/2 cycles for N >= 128, but never fewer than ~44 cycles); three MMAs per K step of 8.
+//
+// One CTA per (subdomain, group of 64 right-hand sides; the groups of a subdomain adjacent in
+// launch order) runs the whole sweep:
 //  - warp 8 (producer) streams the packed factor, chunk by chunk in consumption order, through a
 //    ring of shared-memory stages with cp.async.bulk;
-//  - warp 9 issues, per K step of 8 columns, six MMAs M = 128 (rows of G_k) x N = 2 NRT
-//    ([Re y | Im y]) x K = 8:  P += Gr [Yr|Yi],  Q += Gi [Yr|Yi]  (hi*hi + hi*lo + lo*hi each),
-//    so Re(G y) = P[Yr] - Q[Yi] and Im(G y) = P[Yi] + Q[Yr];
-//  - warps 0-7 (two per TMEM lane quarter, each with half of the right-hand sides) read P and Q
-//    back, apply the sweep's update to the local vectors, and write the next block's operand
-//    (split into hi/lo planes) into shared memory; the values they need for the next block are
-//    loaded while the tensor core works on the current one.
+//  - warp 9 issues the MMAs from precomputed descriptors;
+//  - warps 0-7 read D back (warp w: TMEM lane quarter w % 4 = right-hand sides 16 (w % 4) ..,
+//    column chunks of parity w / 4), combine real and imaginary parts with the partner lane by
+//    shuffle, write the block's t_k or x_k to the local vectors (each thread 4 consecutive rows
+//    of one right-hand side) and the next block's operand rows into shared memory; the values
+//    the next block needs are loaded while the tensor core works on the current one.
+// The accumulation U += x of the DDM steps runs after the kernel as one coalesced pass.
 // Waits are bounded; a time-out sets ERRBIT_TIMEOUT and every role leaves its loop.
 #include <algorithm>
 #include <vector>
@@ -25,36 +35,35 @@
 
 namespace ddm {
 
+constexpr int TC2_NRT = 64;                       // right-hand sides per CTA
 constexpr int TC2_KC = 16;                        // K (columns j of G_k) per pipeline chunk
 constexpr int TC2_NEPI = 8;                       // epilogue warps
 constexpr int TC2_THREADS = (TC2_NEPI + 2) * 32;  // + producer warp + MMA warp
 constexpr int TC2_MAXST = 8;
-// K-direction stride of the operand's core matrices: 144 bytes (128 + 16 of padding) makes the
-// epilogue's writes of one column of the operand (consecutive j) hit 32 distinct banks
-constexpr uint32_t TC2_LBOY = 144;
-// the M = 128 MMA reads 16 row groups of a factor plane; rows past b read whatever follows
-// (their output rows are discarded), so the ring is followed by this much slack
-constexpr uint32_t TC2_TAIL = 8192;
+constexpr int TC2_MAXCH = 8;                      // 8-column chunks per epilogue thread (b <= 128)
+// K-direction stride of the operand's core matrices: 128 bytes (contiguous), so that every
+// 128-byte core matrix the tensor core reads is one aligned shared-memory wavefront
+constexpr uint32_t TC2_LBOA = 128;
 
 long long tc2d_packed_floats(int b, int m) {
   const long long ng = (b + 7) / 8, nKC = (b + TC2_KC - 1) / TC2_KC;
-  return (long long)m * nKC * 4 * ng * 4 * 32;
+  return (long long)m * nKC * 2 * (2 * ng) * 4 * 32;
 }
 
 struct TC2Fac { long long fofs, tofs; int b, m, ldb, pad; };
 
-// packed factor: per block k and chunk kc (16 columns j) the planes {Re hi, Re lo, Im hi, Im lo},
-// each ng row groups x 4 core matrices along K x (8 rows x 4 floats), contiguous
+// packed factor: per block k and chunk kc (16 columns j) two planes {hi, lo} of the 2 bp rows
+// [Re G_k ; Im G_k], each as 2 ng row groups x 4 core matrices along K x (8 rows x 4 floats)
 __global__ void k_g2_pack(const TC2Fac* __restrict__ facs, const c32* __restrict__ G, float* __restrict__ dst) {
   const TC2Fac f = facs[blockIdx.y];
-  const int ng = (f.b + 7) / 8, nKC = (f.b + TC2_KC - 1) / TC2_KC;
-  const long long nI = (long long)ng * 8, nJ = (long long)nKC * TC2_KC;
-  const long long total = (long long)f.m * nJ * nI;
+  const int ng = (f.b + 7) / 8, nKC = (f.b + TC2_KC - 1) / TC2_KC, bp = 8 * ng;
+  const long long nJ = (long long)nKC * TC2_KC;
+  const long long total = (long long)f.m * nJ * bp;
   float* out = dst + f.tofs;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % nI);
-    const long long r = idx / nI;
+    const int i = (int)(idx % bp);
+    const long long r = idx / bp;
     const int j = (int)(r % nJ);
     const int k = (int)(r / nJ);
     c32 v = mk<float>(0.f, 0.f);
@@ -64,12 +73,13 @@ __global__ void k_g2_pack(const TC2Fac* __restrict__ facs, const c32* __restrict
     tc::split_tf32(v.y, ih, il);
     const int kc = j / TC2_KC, jj = j % TC2_KC;
     float* chunk = out + ((long long)k * nKC + kc) * 512 * ng;
-    const int e = ((i >> 3) * 4 + (jj >> 2)) * 32 + (i & 7) * 4 + (jj & 3);
-    const long long ps = 128LL * ng;
-    chunk[e] = rh;
-    chunk[ps + e] = rl;
-    chunk[2 * ps + e] = ih;
-    chunk[3 * ps + e] = il;
+    const long long ps = 256LL * ng;                  // plane: 2 ng groups x 128 floats
+    const int er = ((i >> 3) * 4 + (jj >> 2)) * 32 + (i & 7) * 4 + (jj & 3);            // row i
+    const int ei = (((bp + i) >> 3) * 4 + (jj >> 2)) * 32 + (i & 7) * 4 + (jj & 3);     // row bp + i
+    chunk[er] = rh;
+    chunk[ps + er] = rl;
+    chunk[ei] = ih;
+    chunk[ps + ei] = il;
   }
 }
 
@@ -87,37 +97,41 @@ __device__ __forceinline__ bool epi_any(bool p) {
                : "memory");
   return r != 0;
 }
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void st_shared_v4(uint32_t a, float x, float y, float z, float w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
 
-template <int NRT>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_solve2d_tc(Geom g, const float* __restrict__ gtc, const long long* __restrict__ tcofs,
-                 const c32* __restrict__ src, c32* out, c32* U, int nrhs, int nst, int* err) {
-  constexpr int N = 2 * NRT;          // MMA N: [Re y | Im y]
-  constexpr int NH = NRT / 2;         // right-hand sides per epilogue thread
-  constexpr uint32_t TCOLS = 4 * NRT; // P: columns [0, N), Q: [N, 2N)
+                 const c32* __restrict__ src, c32* out, int nrhs, int nst, int* err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t s_full[TC2_MAXST], s_empty[TC2_MAXST], s_yfull, s_dfull;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
+  __shared__ __align__(16) c32 s_coef[2][128];   // coupling of the next block's operand, per row
   volatile int* abort_flag = &s_abort;
 
   // the right-hand-side groups of one subdomain are adjacent in launch order, so that they run
   // at the same time and the second read of each factor block hits L2
   const SubDesc& s = g.subs[blockIdx.y];
   const int b = s.ext[0], m = s.ext[1];
-  const int ng = (b + 7) / 8, nKC = (b + TC2_KC - 1) / TC2_KC, Kpad = nKC * TC2_KC;
+  const int ng = (b + 7) / 8, bp = 8 * ng, nKC = (b + TC2_KC - 1) / TC2_KC, Kpad = nKC * TC2_KC;
   const int nblk = 2 * m - 1;
-  const int r0 = blockIdx.x * NRT, nr = min(NRT, nrhs - r0);
-  const uint32_t SBOY = (uint32_t)(Kpad / 4) * TC2_LBOY;   // 8-row group stride of the operand
-  const uint32_t YPLANE = (uint32_t)(N / 8) * SBOY;        // one operand plane (hi or lo)
-  const uint32_t STAGE = 2048u * (uint32_t)ng;              // one chunk: 4 planes x ng x 512 bytes
+  const int r0 = blockIdx.x * TC2_NRT, nr = min(TC2_NRT, nrhs - r0);
+  const uint32_t SBOA = (uint32_t)(Kpad / 4) * TC2_LBOA;   // 8-row group stride of the operand
+  const uint32_t APLANE = 16u * SBOA;                       // one operand plane (hi or lo)
+  const uint32_t STAGE = 2048u * (uint32_t)ng;              // one chunk: 2 planes x 2 ng x 512 bytes
   const uint32_t raw = tc::smem_addr(smem_raw);
-  const uint32_t ybase = (raw + 127u) & ~127u;
-  const uint32_t ring = ybase + 2 * YPLANE;
-  unsigned char* ygen = smem_raw + (ybase - raw);
+  const uint32_t abase = (raw + 127u) & ~127u;
+  const uint32_t ring = abase + 2 * APLANE;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), TCOLS);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), 256);
   if (tid == 0) {
     for (int i = 0; i < nst; ++i) {
       tc::bar_init(tc::smem_addr(&s_full[i]), 1);
@@ -128,9 +142,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     s_abort = 0;
     tc::bar_init_fence();
   }
-  // the operand planes start at zero: their K padding (rows j >= b) must stay finite
-  for (uint32_t o = (uint32_t)tid * 16; o < 2 * YPLANE; o += TC2_THREADS * 16)
-    *reinterpret_cast<float4*>(ygen + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+  // the operand planes start at zero: K padding (j >= b) and unused rows must stay finite
+  for (uint32_t o = (uint32_t)tid * 16; o < 2 * APLANE; o += TC2_THREADS * 16) st_shared_v4(abase + o, 0.f, 0.f, 0.f, 0.f);
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
@@ -164,9 +177,13 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   } else if (warp == TC2_NEPI + 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t ID = tc::idesc_tf32(128, N, false);
-      const uint32_t accP = tmem, accQ = tmem + N;
-      const uint32_t PL = 512u * (uint32_t)ng;   // factor plane stride in a stage
+      const uint32_t ID = tc::idesc_tf32(128, 2 * bp, false);
+      // descriptors at the first K step; later steps only move the start address (>> 4)
+      const uint64_t dAh = tc::sdesc(abase, TC2_LBOA, SBOA);
+      const uint64_t dAl = tc::sdesc(abase + APLANE, TC2_LBOA, SBOA);
+      const uint64_t dB = tc::sdesc(ring, 128, 512);
+      const uint64_t BLO = (uint64_t)(1024u * ng) >> 4;    // lo plane of a stage
+      const int nks = (b + 7) / 8;                          // K steps that are not all padding
       long long c = 0;
       bool ok = true;
       for (int bi = 0; bi < nblk && ok; ++bi) {
@@ -179,23 +196,16 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             break;
           }
           tc::fence_after();
-          const uint32_t g0 = ring + (uint32_t)st * STAGE;
+          const uint64_t bst = dB + (((uint64_t)st * STAGE) >> 4);
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             const int ks = 2 * kc + t;
-            if (8 * ks >= b) break;                   // K step entirely in the padding
+            if (ks >= nks) break;
+            const uint64_t ka = (uint64_t)ks * (2 * TC2_LBOA / 16), kb = (uint64_t)t * (256 / 16);
             const uint32_t acc = ks > 0 ? 1u : 0u;
-            const uint64_t Grh = tc::sdesc(g0 + t * 256, 128, 512), Grl = tc::sdesc(g0 + PL + t * 256, 128, 512);
-            const uint64_t Gih = tc::sdesc(g0 + 2 * PL + t * 256, 128, 512);
-            const uint64_t Gil = tc::sdesc(g0 + 3 * PL + t * 256, 128, 512);
-            const uint32_t ya = ybase + (uint32_t)ks * 2 * TC2_LBOY;
-            const uint64_t Yh = tc::sdesc(ya, TC2_LBOY, SBOY), Yl = tc::sdesc(ya + YPLANE, TC2_LBOY, SBOY);
-            tc::mma_tf32(accP, Grh, Yh, ID, acc);
-            tc::mma_tf32(accP, Grh, Yl, ID, 1u);
-            tc::mma_tf32(accP, Grl, Yh, ID, 1u);
-            tc::mma_tf32(accQ, Gih, Yh, ID, acc);
-            tc::mma_tf32(accQ, Gih, Yl, ID, 1u);
-            tc::mma_tf32(accQ, Gil, Yh, ID, 1u);
+            tc::mma_tf32(tmem, dAh + ka, bst + kb, ID, acc);
+            tc::mma_tf32(tmem, dAh + ka, bst + BLO + kb, ID, 1u);
+            tc::mma_tf32(tmem, dAl + ka, bst + kb, ID, 1u);
           }
           tc::mma_commit(tc::smem_addr(&s_empty[st]));
         }
@@ -206,111 +216,129 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------------ epilogue warps 0-7
-    const int i = (warp & 3) * 32 + lane;           // row of the block (TMEM lane)
-    const int hh = warp >> 2;                        // right-hand-side half
-    const bool rowok = i < b;
-    const uint32_t lanebase = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const int q4 = warp & 3, par = warp >> 2;
+    const int n = q4 * 32 + lane;                   // TMEM lane = operand row 2r + a
+    const int r = n >> 1, a = n & 1;                // right-hand side within the group, part
+    const bool rok = r < nr;
+    const uint32_t lanebase = tmem + ((uint32_t)(q4 * 32) << 16);
     const long long lt = g.ltotal, len = (long long)b * m;
     const c32* lc = (const c32*)g.lcoef + s.vofs * 5;   // planes: C, W, E, S, N
     const c32* cSp = lc + 3 * len;
     const c32* cNp = lc + 4 * len;
-    const c32* srcv = src + (long long)r0 * lt + s.vofs;
-    c32* outv = out + (long long)r0 * lt + s.vofs;
-    c32* Uv = U ? U + (long long)r0 * lt + s.vofs : nullptr;
-    const int rh0 = hh * NH;                          // first right-hand side of this thread
-    auto put = [&](int r, c32 y) {                    // operand element (row r, column j = i)
-      float yrh, yrl, yih, yil;
-      tc::split_tf32(y.x, yrh, yrl);
-      tc::split_tf32(y.y, yih, yil);
-      const uint32_t jo = (uint32_t)(i >> 2) * TC2_LBOY + (uint32_t)(i & 3) * 4;
-      const uint32_t ore = (uint32_t)(r >> 3) * SBOY + (uint32_t)(r & 7) * 16 + jo;
-      const uint32_t oim = (uint32_t)((NRT + r) >> 3) * SBOY + (uint32_t)((NRT + r) & 7) * 16 + jo;
-      *reinterpret_cast<float*>(ygen + ore) = yrh;
-      *reinterpret_cast<float*>(ygen + YPLANE + ore) = yrl;
-      *reinterpret_cast<float*>(ygen + oim) = yih;
-      *reinterpret_cast<float*>(ygen + YPLANE + oim) = yil;
+    const long long vo = (long long)(r0 + (rok ? r : 0)) * lt + s.vofs;
+    const c32* srcv = src + vo;
+    c32* outv = out + vo;
+    // this thread's rows of every block: 4 consecutive rows i = 8 cc + 4 a + e (e = 0..3) of its
+    // right-hand side r, for the 8-column chunks cc = par, par + 2, ... < ng
+    const int nch = (ng - par + 1) / 2;
+    // operand row write: rows 2r (real) and 2r+1 (imaginary), columns j = i0 .. i0+3
+    auto put4 = [&](int i0, const c32* y) {
+      float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        tc::split_tf32(y[e].x, rh[e], rl[e]);
+        tc::split_tf32(y[e].y, ih[e], il[e]);
+      }
+      const uint32_t jo = (uint32_t)(i0 >> 2) * TC2_LBOA;
+      const uint32_t ore = abase + (uint32_t)((2 * r) >> 3) * SBOA + (uint32_t)((2 * r) & 7) * 16 + jo;
+      const uint32_t oim = abase + (uint32_t)((2 * r + 1) >> 3) * SBOA + (uint32_t)((2 * r + 1) & 7) * 16 + jo;
+      st_shared_v4(ore, rh[0], rh[1], rh[2], rh[3]);
+      st_shared_v4(ore + APLANE, rl[0], rl[1], rl[2], rl[3]);
+      st_shared_v4(oim, ih[0], ih[1], ih[2], ih[3]);
+      st_shared_v4(oim + APLANE, il[0], il[1], il[2], il[3]);
     };
-    // block 0: y_0 = r_0
-    if (rowok)
-      for (int rr = 0; rr < NH; ++rr)
-        if (rh0 + rr < nr) put(rh0 + rr, srcv[(long long)(rh0 + rr) * lt + i]);
+    // block 0: y_0 = r_0; lane a of the pair writes the rows i = 8 cc + 4 a .. + 3
+    if (rok) {
+      for (int ci = 0; ci < nch; ++ci) {
+        const int i0 = 8 * (par + 2 * ci) + 4 * a;
+        c32 y[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y[e] = i0 + e < b ? srcv[i0 + e] : mk<float>(0.f, 0.f);
+        put4(i0, y);
+      }
+    }
     tc::fence_async_smem();
     epi_sync();
     if (tid == 0) tc::bar_arrive(tc::smem_addr(&s_yfull));
-    // values the epilogue of block bi needs, loaded one block ahead:
-    //   pass 0: pa = r_{k+1} (next block's source), pb = U_k at k = m-1
-    //   pass 1: pa = t_k, pb = U_k;  pc = coupling of the next block's operand
-    c32 pa[NH], pb[NH];
-    c32 pc = mk<float>(0.f, 0.f);
+    // values the epilogue of block bi needs, loaded one block ahead (4 rows per chunk):
+    //   pass 0: pa = r_{k+1} (next block's source);  pass 1: pa = t_k
+    c32 pa[TC2_MAXCH][4];
     auto prefetch = [&](int bi) {
       int pass, k;
       seq2(bi, m, pass, k);
-      const bool upd = Uv && (pass == 1 || k == m - 1);
-      const long long o = (long long)k * b + i;
-      if (rowok) {
-        if (bi + 1 < nblk) pc = pass == 0 ? (k + 1 < m ? cSp[o + b] : cNp[o - b]) : cNp[o - b];
+      const bool need = rok && (pass == 1 || k + 1 < m);
+      const long long o = pass == 0 ? (long long)(k + 1) * b : (long long)k * b;
+      const c32* p = pass == 0 ? srcv : outv;
 #pragma unroll
-        for (int rr = 0; rr < NH; ++rr) {
-          const long long ro = (long long)(rh0 + rr) * lt;
-          const bool ok = rh0 + rr < nr;
-          pa[rr] = (ok && (pass == 1 || k + 1 < m)) ? (pass == 0 ? srcv[ro + o + b] : outv[ro + o]) : mk<float>(0.f, 0.f);
-          pb[rr] = (ok && upd) ? Uv[ro + o] : mk<float>(0.f, 0.f);
-        }
+      for (int ci = 0; ci < TC2_MAXCH; ++ci) {
+        const int i0 = 8 * (par + 2 * ci) + 4 * a;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          pa[ci][e] = (need && ci < nch && i0 + e < b) ? p[o + i0 + e] : mk<float>(0.f, 0.f);
       }
     };
-    // the values of block bi + 2 are pulled into L2 while block bi + 1's are loaded
-    auto prefetch_l2 = [&](int bi) {
-      if (bi >= nblk || !rowok) return;
-      int pass, k;
-      seq2(bi, m, pass, k);
-      const long long o = (long long)k * b + i;
-      const bool upd = Uv && (pass == 1 || k == m - 1);
-#pragma unroll
-      for (int rr = 0; rr < NH; ++rr) {
-        if (rh0 + rr >= nr) break;
-        const long long ro = (long long)(rh0 + rr) * lt;
-        if (pass == 1) tc::prefetch_l2(outv + ro + o);
-        else if (k + 1 < m) tc::prefetch_l2(srcv + ro + o + b);
-        if (upd) tc::prefetch_l2(Uv + ro + o);
-      }
+    // couplings of the operand of block bi + 1, used by the epilogue of block bi, copied
+    // asynchronously into s_coef[bi & 1] one block ahead
+    auto coef_copy = [&](int bi) {
+      if (bi + 1 >= nblk) return;
+      int npass, nk;
+      seq2(bi + 1, m, npass, nk);
+      const c32* cp = npass == 0 ? cSp + (long long)nk * b : cNp + (long long)nk * b;
+      if (tid < b) cp_async8(tc::smem_addr(&s_coef[bi & 1][tid]), cp + tid);
+      cp_async_commit();
     };
     prefetch(0);
-    prefetch_l2(1);
+    coef_copy(0);
     for (int bi = 0; bi < nblk; ++bi) {
       int pass, k;
       seq2(bi, m, pass, k);
-      // one thread waits for the accumulators; the others sleep in the barrier
+      // one thread waits for the accumulators; the others sleep in the barrier, which also makes
+      // every thread's coefficient copies visible
+      cp_async_wait_all();
       bool got = true;
       if (tid == 0) got = tc::bar_wait_or_abort(tc::smem_addr(&s_dfull), (uint32_t)(bi & 1), abort_flag);
       if (epi_any(!got)) break;
       tc::fence_after();
-      const bool upd = Uv && (pass == 1 || k == m - 1);
       const bool more = bi + 1 < nblk;
       int npass = 0, nk = 0;
       if (more) seq2(bi + 1, m, npass, nk);
+      const c32* cnext = s_coef[bi & 1];
+      const long long ko = (long long)k * b;
 #pragma unroll
-      for (int c0 = 0; c0 < NH; c0 += 8) {
-        const uint32_t col = (uint32_t)(rh0 + c0);
-        uint32_t pr[8], pim[8], qr[8], qim[8];
-        tc::tmem_ld8_async(lanebase + col, pr);             // Gr Yr
-        tc::tmem_ld8_async(lanebase + NRT + col, pim);      // Gr Yi
-        tc::tmem_ld8_async(lanebase + N + col, qr);         // Gi Yr
-        tc::tmem_ld8_async(lanebase + N + NRT + col, qim);  // Gi Yi
+      for (int ci = 0; ci < TC2_MAXCH; ++ci) {
+        if (ci >= nch) break;                          // warp-uniform
+        const int cc = par + 2 * ci;
+        uint32_t u0[8], u1[8];
+        tc::tmem_ld8_async(lanebase + (uint32_t)(8 * cc), u0);        // Y_a G_r, columns 8cc..
+        tc::tmem_ld8_async(lanebase + (uint32_t)(bp + 8 * cc), u1);   // Y_a G_i
         tc::tmem_wait_ld();
-        if (rowok) {
+        // this lane's 4 rows i = 8 cc + 4 a + e; the partner lane holds the other part of y
+        c32 y[4];
+        const int i0 = 8 * cc + 4 * a;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int rr = c0 + j, r = rh0 + rr;
-            if (r >= nr) continue;
-            const c32 C = mk<float>(__uint_as_float(pr[j]) - __uint_as_float(qim[j]),
-                                    __uint_as_float(pim[j]) + __uint_as_float(qr[j]));
-            const c32 v = pass == 0 ? C : pa[rr] - C;           // t_k, or x_k = t_k - G_k z
-            const long long o = (long long)r * lt + (long long)k * b + i;
-            outv[o] = v;
-            if (upd) Uv[o] = pb[rr] + v;
-            if (more) put(r, npass == 0 ? pa[rr] - pc * v : pc * v);
+        for (int e = 0; e < 4; ++e) {
+          // lane a keeps rows 4a..4a+3 of the chunk and sends the partner its other four
+          const float x0 = __uint_as_float(a == 0 ? u0[e] : u0[4 + e]);
+          const float x1 = __uint_as_float(a == 0 ? u1[e] : u1[4 + e]);
+          const float s0 = __uint_as_float(a == 0 ? u0[4 + e] : u0[e]);
+          const float s1 = __uint_as_float(a == 0 ? u1[4 + e] : u1[e]);
+          const float w0 = __shfl_xor_sync(0xffffffffu, s0, 1);   // partner's Y G_r at my row
+          const float w1 = __shfl_xor_sync(0xffffffffu, s1, 1);   // partner's Y G_i at my row
+          // even lane: x = (Yr Gr, Yr Gi), w = (Yi Gr, Yi Gi); odd lane: the reverse
+          const float yrgr = a == 0 ? x0 : w0, yrgi = a == 0 ? x1 : w1;
+          const float yigr = a == 0 ? w0 : x0, yigi = a == 0 ? w1 : x1;
+          const c32 C = mk<float>(yrgr - yigi, yrgi + yigr);
+          const int i = i0 + e;
+          const c32 v = pass == 0 ? C : pa[ci][e] - C;          // t_k, or x_k = t_k - G_k z
+          if (rok && i < b) outv[ko + i] = v;
+          c32 yv = mk<float>(0.f, 0.f);
+          if (more && i < b) {
+            const c32 cf = cnext[i];   // shared memory
+            yv = npass == 0 ? pa[ci][e] - cf * v : cf * v;
           }
+          y[e] = yv;
         }
+        if (more && rok) put4(i0, y);
       }
       tc::fence_before();
       tc::fence_async_smem();
@@ -318,13 +346,33 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
       if (more) {
         if (tid == 0) tc::bar_arrive(tc::smem_addr(&s_yfull));
         prefetch(bi + 1);
-        prefetch_l2(bi + 2);
+        coef_copy(bi + 1);
       }
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, TCOLS);
+  if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
+// U += x over the local vectors of nrhs right-hand sides (n complex values; 16-byte steps when
+// both arrays are 16-byte aligned)
+__global__ void k_accum_local(c32* __restrict__ U, const c32* __restrict__ x, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
+  if (vec) {
+    float4* U4 = reinterpret_cast<float4*>(U);
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n / 2; i += stride) {
+      float4 u = U4[i];
+      const float4 v = x4[i];
+      u.x += v.x; u.y += v.y; u.z += v.z; u.w += v.w;
+      U4[i] = u;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) U[n - 1] = U[n - 1] + x[n - 1];
+  } else {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) U[i] = U[i] + x[i];
+  }
 }
 
 // ------------------------------------------------------------------------------------ host
@@ -358,54 +406,45 @@ cudaError_t tc2d_pack_factors(ddm_ctx* c) {
   return e;
 }
 
-// shared memory of the solve for NRT right-hand sides per CTA; 0 if fewer than two stages fit
-template <int NRT>
+// shared memory of the solve; 0 if the blocks are too wide or fewer than two ring stages fit
 static size_t tc2d_smem(const ddm_ctx* c, int* nst_out) {
   int bmax = 0;
   for (auto& s : c->subs) bmax = std::max(bmax, s.ext[0]);
   const size_t ng = (bmax + 7) / 8, Kpad = (size_t)((bmax + TC2_KC - 1) / TC2_KC) * TC2_KC;
-  const size_t yplane = (size_t)(2 * NRT / 8) * (Kpad / 4) * TC2_LBOY;
+  const size_t aplane = 16 * (Kpad / 4) * TC2_LBOA;
   const size_t stage = 2048 * ng;
-  const size_t fixed = 128 + 2 * yplane + TC2_TAIL;
-  const size_t limit = 227 * 1024;
-  if (fixed + 2 * stage > limit) return 0;
+  const size_t fixed = 128 + 2 * aplane;
+  const size_t limit = 227 * 1024 - 4096;   // the kernel's static shared memory beside it
+  if (bmax > 16 * TC2_MAXCH || fixed + 2 * stage > limit) return 0;
   const int nst = (int)std::min<size_t>(TC2_MAXST, (limit - fixed) / stage);
   *nst_out = nst;
   return fixed + (size_t)nst * stage;
 }
 
-template <int NRT>
-static cudaError_t tc2d_solve_n(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
-  int nst = 0;
-  const size_t sm = tc2d_smem<NRT>(c, &nst);
-  if (!sm) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_solve2d_tc<NRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  dim3 grid((nrhs + NRT - 1) / NRT, c->g.nsub);
-  ++c->nlaunch;
-  k_solve2d_tc<NRT><<<grid, TC2_THREADS, sm, c->st>>>(c->g, c->d_gtc2, c->d_tc2ofs, (const c32*)src, (c32*)out,
-                                                      (c32*)U, nrhs, nst, c->d_err);
-  return cudaGetLastError();
-}
-
 bool tc2d_supported(const ddm_ctx* c, int nrt) {
   int nst = 0;
-  if (!c->d_gtc2) return false;
-  switch (nrt) {
-    case 16: return tc2d_smem<16>(c, &nst) > 0;
-    case 32: return tc2d_smem<32>(c, &nst) > 0;
-    case 64: return tc2d_smem<64>(c, &nst) > 0;
-    default: return false;
-  }
+  return c->d_gtc2 && nrt == TC2_NRT && tc2d_smem(c, &nst) > 0;
 }
 
 cudaError_t tc2d_solve(ddm_ctx* c, int nrt, const void* src, void* out, void* U, int nrhs) {
-  switch (nrt) {
-    case 16: return tc2d_solve_n<16>(c, src, out, U, nrhs);
-    case 32: return tc2d_solve_n<32>(c, src, out, U, nrhs);
-    case 64: return tc2d_solve_n<64>(c, src, out, U, nrhs);
-    default: return cudaErrorInvalidValue;
+  if (nrt != TC2_NRT) return cudaErrorInvalidValue;
+  int nst = 0;
+  const size_t sm = tc2d_smem(c, &nst);
+  if (!sm) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_solve2d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nrhs + TC2_NRT - 1) / TC2_NRT, c->g.nsub);
+  ++c->nlaunch;
+  k_solve2d_tc<<<grid, TC2_THREADS, sm, c->st>>>(c->g, c->d_gtc2, c->d_tc2ofs, (const c32*)src, (c32*)out, nrhs,
+                                                 nst, c->d_err);
+  if (U) {
+    // after the backward sweep `out` holds the solution of every block: U += out in one pass
+    const long long n = c->g.ltotal * nrhs;
+    ++c->nlaunch;
+    k_accum_local<<<(int)std::min<long long>((n / 2 + 255) / 256, 152LL * 32), 256, 0, c->st>>>((c32*)U,
+                                                                                               (const c32*)out, n);
   }
+  return cudaGetLastError();
 }
 
 }  // namespace ddm

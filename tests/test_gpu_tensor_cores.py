@@ -118,7 +118,7 @@ def _local2d(wl, nrhs, nr, seed=7):
 
 
 @pytest.mark.parametrize("name", list(CASES2D))
-@pytest.mark.parametrize("nr,nrhs", [(16, 16), (16, 21), (32, 40), (64, 64), (64, 37)])
+@pytest.mark.parametrize("nr,nrhs", [(64, 16), (64, 21), (64, 64), (64, 37), (64, 70)])
 def test_2d_tensor_core_local_solves_match_oracle(name, nr, nrhs):
     wl = CASES2D[name]
     o, srcs, tc = _local2d(wl, nrhs, nr)
@@ -146,21 +146,21 @@ def test_2d_tensor_core_accumulates_U_like_cuda_cores():
     o = oracle_of(wl)
     b = np.stack([o.rhs(wl.f[r]) for r in range(16)])
     res = {}
-    for nr in (16, 2):
+    for nr in (64, 2):
         s = D.Solver(wl, precision=D.DDM_MIXED, max_rhs=16).factor()
         D.ddm_set_rhs_per_cta(s.ctx, nr)
         w = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
         D.ddm_apply(s.ctx, 5, s.to_dev(b), w, 16)
         res[nr] = w.cpu().numpy()
         s.close()
-    assert rel(res[16], res[2]) < 1e-4
+    assert rel(res[64], res[2]) < 1e-4
 
 
 def test_2d_tensor_core_fgmres_batched_reaches_1e6():
     wl = W.tiny_2d(seed=25, n=40, parts=(2, 2), ov=2, npml=8, nrhs=20)
     o = oracle_of(wl)
     s = D.Solver(wl, precision=D.DDM_MIXED, max_rhs=20).factor()
-    D.ddm_set_rhs_per_cta(s.ctx, 32)
+    D.ddm_set_rhs_per_cta(s.ctx, 64)
     u = torch.zeros(wl.f.shape, dtype=torch.complex128, device="cuda")
     info = D.ddm_solve(s.ctx, s.to_dev(wl.f), u, nrhs=20, tol=1e-6, max_it=200, mode=D.DDM_FGMRES, K=4,
                        restart=30)
@@ -176,9 +176,9 @@ def test_rhs_per_cta_validation():
     wl = W.tiny_2d(seed=26, n=16, parts=(2, 2), ov=1, npml=3)
     s = D.Solver(wl, precision=D.DDM_MIXED, max_rhs=4).factor()     # max_rhs < 16: nothing packed
     with pytest.raises(D.DDMError):
-        D.ddm_set_rhs_per_cta(s.ctx, 16)
+        D.ddm_set_rhs_per_cta(s.ctx, 64)
     with pytest.raises(D.DDMError):
-        D.ddm_set_rhs_per_cta(s.ctx, 3)
+        D.ddm_set_rhs_per_cta(s.ctx, 16)
     D.ddm_set_rhs_per_cta(s.ctx, 4)
     D.ddm_set_rhs_per_cta(s.ctx, 0)
     s.close()

@@ -7,8 +7,8 @@
 // G_k with a b x 64 operand, done here on the 5th-generation tensor cores in split TF32
 // ("3xTF32": x = hi + lo with hi = tf32(x); hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor
 // memory, FP32-level accuracy) as ONE real product per split term:
-//   A (M = 128 rows): row 2r + a is the real (a = 0) or imaginary (a = 1) part of right-hand
-//     side r's block vector, K = the b columns j;
+//   A (M = 128 rows, in tensor memory): row 2r + a is the real (a = 0) or imaginary (a = 1)
+//     part of right-hand side r's block vector, K = the b columns j;
 //   B (N = 2 bp rows, bp = b rounded up to 8): rows [Re G_k ; Im G_k], K = j;
 //   D = A B^T in tensor memory: D[2r+a][c bp + i] = sum_j Y_a(r, j) G_c(i, j),
 // so that Re(G y) = D[2r][i] - D[2r+1][bp+i] and Im(G y) = D[2r][bp+i] + D[2r+1][i].  N = 2 bp
@@ -23,8 +23,10 @@
 //  - warps 0-7 read D back (warp w: TMEM lane quarter w % 4 = right-hand sides 16 (w % 4) ..,
 //    column chunks of parity w / 4), combine real and imaginary parts with the partner lane by
 //    shuffle, write the block's t_k or x_k to the local vectors (each thread 4 consecutive rows
-//    of one right-hand side) and the next block's operand rows into shared memory; the values
-//    the next block needs are loaded while the tensor core works on the current one.
+//    of one right-hand side) and the next block's operand row (its own TMEM lane) with
+//    tcgen05.st; the values the next block needs are loaded while the tensor core works on the
+//    current one.  Tensor memory: D in columns [0, 2 bp), operand hi in [256, 256 + bp), lo in
+//    [384, 384 + bp); shared memory holds only the factor ring.
 // The accumulation U += x of the DDM steps runs after the kernel as one coalesced pass.
 // Waits are bounded; a time-out sets ERRBIT_TIMEOUT and every role leaves its loop.
 #include <algorithm>
@@ -36,24 +38,25 @@
 namespace ddm {
 
 constexpr int TC2_NRT = 64;                       // right-hand sides per CTA
-constexpr int TC2_KC = 16;                        // K (columns j of G_k) per pipeline chunk
+constexpr int TC2_KC = 32;                        // K (columns j of G_k) per pipeline chunk
+constexpr int TC2_KCC = TC2_KC / 4;               // core matrices along K per chunk
+constexpr int TC2_KSTEPS = TC2_KC / 8;            // tf32 MMA K steps per chunk
 constexpr int TC2_NEPI = 8;                       // epilogue warps
 constexpr int TC2_THREADS = (TC2_NEPI + 2) * 32;  // + producer warp + MMA warp
 constexpr int TC2_MAXST = 8;
 constexpr int TC2_MAXCH = 8;                      // 8-column chunks per epilogue thread (b <= 128)
-// K-direction stride of the operand's core matrices: 128 bytes (contiguous), so that every
-// 128-byte core matrix the tensor core reads is one aligned shared-memory wavefront
-constexpr uint32_t TC2_LBOA = 128;
+constexpr uint32_t TC2_AH = 256, TC2_AL = 384;    // TMEM columns of the operand's hi and lo parts
+constexpr uint32_t TC2_TCOLS = 512;               // TMEM columns allocated (and freed) per CTA
 
 long long tc2d_packed_floats(int b, int m) {
   const long long ng = (b + 7) / 8, nKC = (b + TC2_KC - 1) / TC2_KC;
-  return (long long)m * nKC * 2 * (2 * ng) * 4 * 32;
+  return (long long)m * nKC * 2 * (2 * ng) * TC2_KCC * 32;
 }
 
 struct TC2Fac { long long fofs, tofs; int b, m, ldb, pad; };
 
-// packed factor: per block k and chunk kc (16 columns j) two planes {hi, lo} of the 2 bp rows
-// [Re G_k ; Im G_k], each as 2 ng row groups x 4 core matrices along K x (8 rows x 4 floats)
+// packed factor: per block k and chunk kc (TC2_KC columns j) two planes {hi, lo} of the 2 bp rows
+// [Re G_k ; Im G_k], each as 2 ng row groups x TC2_KCC core matrices along K x (8 rows x 4 floats)
 __global__ void k_g2_pack(const TC2Fac* __restrict__ facs, const c32* __restrict__ G, float* __restrict__ dst) {
   const TC2Fac f = facs[blockIdx.y];
   const int ng = (f.b + 7) / 8, nKC = (f.b + TC2_KC - 1) / TC2_KC, bp = 8 * ng;
@@ -72,10 +75,10 @@ __global__ void k_g2_pack(const TC2Fac* __restrict__ facs, const c32* __restrict
     tc::split_tf32(v.x, rh, rl);
     tc::split_tf32(v.y, ih, il);
     const int kc = j / TC2_KC, jj = j % TC2_KC;
-    float* chunk = out + ((long long)k * nKC + kc) * 512 * ng;
-    const long long ps = 256LL * ng;                  // plane: 2 ng groups x 128 floats
-    const int er = ((i >> 3) * 4 + (jj >> 2)) * 32 + (i & 7) * 4 + (jj & 3);            // row i
-    const int ei = (((bp + i) >> 3) * 4 + (jj >> 2)) * 32 + (i & 7) * 4 + (jj & 3);     // row bp + i
+    const long long ps = 64LL * ng * TC2_KCC;          // plane: 2 ng groups x TC2_KCC x 32 floats
+    float* chunk = out + ((long long)k * nKC + kc) * 2 * ps;
+    const int er = ((i >> 3) * TC2_KCC + (jj >> 2)) * 32 + (i & 7) * 4 + (jj & 3);            // row i
+    const int ei = (((bp + i) >> 3) * TC2_KCC + (jj >> 2)) * 32 + (i & 7) * 4 + (jj & 3);     // row bp + i
     chunk[er] = rh;
     chunk[ps + er] = rl;
     chunk[ei] = ih;
@@ -102,9 +105,6 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void st_shared_v4(uint32_t a, float x, float y, float z, float w) {
-  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
-}
 
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_solve2d_tc(Geom g, const float* __restrict__ gtc, const long long* __restrict__ tcofs,
@@ -120,18 +120,15 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   // at the same time and the second read of each factor block hits L2
   const SubDesc& s = g.subs[blockIdx.y];
   const int b = s.ext[0], m = s.ext[1];
-  const int ng = (b + 7) / 8, bp = 8 * ng, nKC = (b + TC2_KC - 1) / TC2_KC, Kpad = nKC * TC2_KC;
+  const int ng = (b + 7) / 8, bp = 8 * ng, nKC = (b + TC2_KC - 1) / TC2_KC;
   const int nblk = 2 * m - 1;
   const int r0 = blockIdx.x * TC2_NRT, nr = min(TC2_NRT, nrhs - r0);
-  const uint32_t SBOA = (uint32_t)(Kpad / 4) * TC2_LBOA;   // 8-row group stride of the operand
-  const uint32_t APLANE = 16u * SBOA;                       // one operand plane (hi or lo)
-  const uint32_t STAGE = 2048u * (uint32_t)ng;              // one chunk: 2 planes x 2 ng x 512 bytes
+  const uint32_t STAGE = 512u * TC2_KCC * (uint32_t)ng;     // one chunk: 2 planes x 2 ng groups
   const uint32_t raw = tc::smem_addr(smem_raw);
-  const uint32_t abase = (raw + 127u) & ~127u;
-  const uint32_t ring = abase + 2 * APLANE;
+  const uint32_t ring = (raw + 127u) & ~127u;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), 256);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), TC2_TCOLS);
   if (tid == 0) {
     for (int i = 0; i < nst; ++i) {
       tc::bar_init(tc::smem_addr(&s_full[i]), 1);
@@ -142,13 +139,19 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     s_abort = 0;
     tc::bar_init_fence();
   }
-  // the operand planes start at zero: K padding (j >= b) and unused rows must stay finite
-  for (uint32_t o = (uint32_t)tid * 16; o < 2 * APLANE; o += TC2_THREADS * 16) st_shared_v4(abase + o, 0.f, 0.f, 0.f, 0.f);
-  tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = s_tmem;
+  // the operand columns start at zero (unused rows stay finite)
+  if (warp < 4) {
+    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t c0 = TC2_AH; c0 < TC2_TCOLS; c0 += 8) tc::tmem_st8(tmem + ((uint32_t)(warp * 32) << 16) + c0, z);
+    tc::tmem_wait_st();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
 
   if (warp == TC2_NEPI) {
     // ------------------------------------------------------------------ producer
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
           }
           const uint32_t fb = tc::smem_addr(&s_full[st]);
           tc::bar_expect_tx(fb, STAGE);
-          tc::bulk_load(ring + (uint32_t)st * STAGE, gsrc + ((long long)k * nKC + kc) * 512 * ng, STAGE, fb);
+          tc::bulk_load(ring + (uint32_t)st * STAGE, gsrc + ((long long)k * nKC + kc) * (STAGE / 4), STAGE, fb);
         }
       }
       // the copies still in flight land before the CTA may exit (bounded)
@@ -178,11 +181,9 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t ID = tc::idesc_tf32(128, 2 * bp, false);
-      // descriptors at the first K step; later steps only move the start address (>> 4)
-      const uint64_t dAh = tc::sdesc(abase, TC2_LBOA, SBOA);
-      const uint64_t dAl = tc::sdesc(abase + APLANE, TC2_LBOA, SBOA);
-      const uint64_t dB = tc::sdesc(ring, 128, 512);
-      const uint64_t BLO = (uint64_t)(1024u * ng) >> 4;    // lo plane of a stage
+      // descriptor at the first stage and K step; others only move the start address (>> 4)
+      const uint64_t dB = tc::sdesc(ring, 128, 128 * TC2_KCC);
+      const uint64_t BLO = (uint64_t)(STAGE / 2) >> 4;     // lo plane of a stage
       const int nks = (b + 7) / 8;                          // K steps that are not all padding
       long long c = 0;
       bool ok = true;
@@ -198,14 +199,15 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
           tc::fence_after();
           const uint64_t bst = dB + (((uint64_t)st * STAGE) >> 4);
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const int ks = 2 * kc + t;
+          for (int t = 0; t < TC2_KSTEPS; ++t) {
+            const int ks = TC2_KSTEPS * kc + t;
             if (ks >= nks) break;
-            const uint64_t ka = (uint64_t)ks * (2 * TC2_LBOA / 16), kb = (uint64_t)t * (256 / 16);
+            const uint32_t ka = (uint32_t)(8 * ks);
+            const uint64_t kb = (uint64_t)t * (256 / 16);
             const uint32_t acc = ks > 0 ? 1u : 0u;
-            tc::mma_tf32(tmem, dAh + ka, bst + kb, ID, acc);
-            tc::mma_tf32(tmem, dAh + ka, bst + BLO + kb, ID, 1u);
-            tc::mma_tf32(tmem, dAl + ka, bst + kb, ID, 1u);
+            tc::mma_tf32_ts(tmem, tmem + TC2_AH + ka, bst + kb, ID, acc);
+            tc::mma_tf32_ts(tmem, tmem + TC2_AH + ka, bst + BLO + kb, ID, 1u);
+            tc::mma_tf32_ts(tmem, tmem + TC2_AL + ka, bst + kb, ID, 1u);
           }
           tc::mma_commit(tc::smem_addr(&s_empty[st]));
         }
@@ -231,33 +233,28 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     // this thread's rows of every block: 4 consecutive rows i = 8 cc + 4 a + e (e = 0..3) of its
     // right-hand side r, for the 8-column chunks cc = par, par + 2, ... < ng
     const int nch = (ng - par + 1) / 2;
-    // operand row write: rows 2r (real) and 2r+1 (imaginary), columns j = i0 .. i0+3
-    auto put4 = [&](int i0, const c32* y) {
-      float rh[4], rl[4], ih[4], il[4];
+    // operand row write: this lane's row (part a of right-hand side r), columns j = 8 cc .. + 7
+    auto put8 = [&](int cc, const float* v) {
+      float hi[8], lo[8];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        tc::split_tf32(y[e].x, rh[e], rl[e]);
-        tc::split_tf32(y[e].y, ih[e], il[e]);
-      }
-      const uint32_t jo = (uint32_t)(i0 >> 2) * TC2_LBOA;
-      const uint32_t ore = abase + (uint32_t)((2 * r) >> 3) * SBOA + (uint32_t)((2 * r) & 7) * 16 + jo;
-      const uint32_t oim = abase + (uint32_t)((2 * r + 1) >> 3) * SBOA + (uint32_t)((2 * r + 1) & 7) * 16 + jo;
-      st_shared_v4(ore, rh[0], rh[1], rh[2], rh[3]);
-      st_shared_v4(ore + APLANE, rl[0], rl[1], rl[2], rl[3]);
-      st_shared_v4(oim, ih[0], ih[1], ih[2], ih[3]);
-      st_shared_v4(oim + APLANE, il[0], il[1], il[2], il[3]);
+      for (int e = 0; e < 8; ++e) tc::split_tf32(v[e], hi[e], lo[e]);
+      tc::tmem_st8(lanebase + TC2_AH + (uint32_t)(8 * cc), hi);
+      tc::tmem_st8(lanebase + TC2_AL + (uint32_t)(8 * cc), lo);
     };
-    // block 0: y_0 = r_0; lane a of the pair writes the rows i = 8 cc + 4 a .. + 3
-    if (rok) {
-      for (int ci = 0; ci < nch; ++ci) {
-        const int i0 = 8 * (par + 2 * ci) + 4 * a;
-        c32 y[4];
+    // block 0: y_0 = r_0
+    for (int ci = 0; ci < nch; ++ci) {
+      const int cc = par + 2 * ci;
+      float v[8];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) y[e] = i0 + e < b ? srcv[i0 + e] : mk<float>(0.f, 0.f);
-        put4(i0, y);
+      for (int e = 0; e < 8; ++e) {
+        const int i = 8 * cc + e;
+        const c32 y = (rok && i < b) ? srcv[i] : mk<float>(0.f, 0.f);
+        v[e] = a == 0 ? y.x : y.y;
       }
+      put8(cc, v);
     }
-    tc::fence_async_smem();
+    tc::tmem_wait_st();
+    tc::fence_before();
     epi_sync();
     if (tid == 0) tc::bar_arrive(tc::smem_addr(&s_yfull));
     // values the epilogue of block bi needs, loaded one block ahead (4 rows per chunk):
@@ -338,10 +335,23 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
           }
           y[e] = yv;
         }
-        if (more && rok) put4(i0, y);
+        if (more) {
+          // row values of the next operand: part a of y at the chunk's 8 rows; the partner lane
+          // holds the other 4 rows
+          float send[4], v8[8];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) send[e] = a == 0 ? y[e].y : y[e].x;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float recv = __shfl_xor_sync(0xffffffffu, send[e], 1);
+            v8[e] = a == 0 ? y[e].x : recv;
+            v8[4 + e] = a == 0 ? recv : y[e].y;
+          }
+          put8(cc, v8);
+        }
       }
+      tc::tmem_wait_st();
       tc::fence_before();
-      tc::fence_async_smem();
       epi_sync();
       if (more) {
         if (tid == 0) tc::bar_arrive(tc::smem_addr(&s_yfull));
@@ -352,7 +362,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 256);
+  if (warp == 0) tc::tmem_free(tmem, TC2_TCOLS);
 }
 
 // U += x over the local vectors of nrhs right-hand sides (n complex values; 16-byte steps when
@@ -410,10 +420,9 @@ cudaError_t tc2d_pack_factors(ddm_ctx* c) {
 static size_t tc2d_smem(const ddm_ctx* c, int* nst_out) {
   int bmax = 0;
   for (auto& s : c->subs) bmax = std::max(bmax, s.ext[0]);
-  const size_t ng = (bmax + 7) / 8, Kpad = (size_t)((bmax + TC2_KC - 1) / TC2_KC) * TC2_KC;
-  const size_t aplane = 16 * (Kpad / 4) * TC2_LBOA;
-  const size_t stage = 2048 * ng;
-  const size_t fixed = 128 + 2 * aplane;
+  const size_t ng = (bmax + 7) / 8;
+  const size_t stage = 512 * TC2_KCC * ng;
+  const size_t fixed = 128;
   const size_t limit = 227 * 1024 - 4096;   // the kernel's static shared memory beside it
   if (bmax > 16 * TC2_MAXCH || fixed + 2 * stage > limit) return 0;
   const int nst = (int)std::min<size_t>(TC2_MAXST, (limit - fixed) / stage);

@@ -35,6 +35,7 @@ constexpr int TC3_PLANE = TC3_TILE * TC3_KC;   // floats per plane of a block (4
 constexpr int TC3_BLOCK = 4 * TC3_PLANE;       // floats per block (16 KB)
 constexpr int TC3_NST = 6;                     // ring stages, 32 KB each
 constexpr int TC3_SMEM = TC3_NST * 2 * TC3_BLOCK * 4 + 1024;
+constexpr uint32_t TC3_TCOLS = 256;            // TMEM columns allocated (and freed) per CTA
 
 // packed factor of one plane: blocks (it, kc), it < nIT, kc < nKC
 __global__ void k_g3_pack(const c32* __restrict__ G, long long fofs, int ldb, int b, int m, int nIT, int nKC,
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t dsm = (tc::smem_addr(dsm_raw) + 1023u) & ~1023u;
   const uint32_t STAGE_BYTES = 2 * TC3_BLOCK * 4;
 
-  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), 256);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), TC3_TCOLS);
   if (tid == 0) {
     for (int s = 0; s < TC3_NST; ++s) {
       tc::bar_init(tc::smem_addr(&s_full[s]), 1);
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 256);
+  if (warp == 0) tc::tmem_free(tmem, TC3_TCOLS);
 }
 
 // Epilogue of plane step (pass, k): one thread per (tile, q, i), consecutive threads along i.

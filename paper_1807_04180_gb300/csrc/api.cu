@@ -405,8 +405,14 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   }
   c->nfac = (int)reps.size();
   c->fac_elems = ofs;
-  if (c->d_G) { cudaFree(c->d_G); c->d_G = nullptr; }
-  CK(cudaMalloc(&c->d_G, ofs * local_elem(c)));
+  const size_t gbytes = (size_t)ofs * local_elem(c);
+  if (gbytes > c->G_cap) {
+    if (c->d_G) { cudaFree(c->d_G); c->d_G = nullptr; }
+    c->G_cap = 0;
+    c->drop_graphs();
+    CK(cudaMalloc(&c->d_G, gbytes));
+    c->G_cap = gbytes;
+  }
   CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDesc) * g.nsub, cudaMemcpyHostToDevice, c->st));
   int *d_reps = nullptr, *d_ldb = nullptr;
   long long* d_fofs = nullptr;
@@ -922,6 +928,7 @@ extern "C" ddm_status ddm_set_graph(ddm_ctx* c, int enable) {
 
 extern "C" ddm_status ddm_set_tensor_cores(ddm_ctx* c, int enable) {
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (c->use_tc != (enable != 0)) c->drop_graphs();   // captured graphs hold the kernel choice
   c->use_tc = enable != 0;
   return DDM_OK;
 }
@@ -935,6 +942,7 @@ extern "C" ddm_status ddm_set_rhs_per_cta(ddm_ctx* c, int nr) {
     return fail(c, DDM_E_INVAL,
                 "64 right-hand sides per CTA run on the tensor cores: 2D, DDM_MIXED, max_rhs >= 16, factored, "
                 "blocks of at most 128 rows whose operand and two ring stages fit in shared memory");
+  if (c->forced_nr != nr) c->drop_graphs();
   c->forced_nr = nr;
   return DDM_OK;
 }

@@ -163,8 +163,9 @@ struct ddm_ctx {
   long long npart = 0;
   double* d_scal = nullptr;      // small device scalars (norms, Krylov coefficients)
   double* h_scal = nullptr;      // pinned host mirror
-  // factors
+  // factors (grow-only buffers: graphs of M_K keep their addresses)
   void* d_G = nullptr;
+  size_t G_cap = 0;              // bytes
   int nfac = 0;
   std::vector<int> fac_b, fac_m, fac_ldb;
   std::vector<long long> fac_ofs;
@@ -197,6 +198,7 @@ struct ddm_ctx {
   // the packed operand of the current plane step
   bool use_tc = true;
   float* d_gtc = nullptr;
+  size_t gtc_cap = 0;            // floats
   std::vector<long long> tc_ofs;
   float* d_ytc = nullptr;
   size_t ytc_cap = 0;
@@ -206,6 +208,7 @@ struct ddm_ctx {
   // factors (written by ddm_factor when max_rhs >= 16) and their per-factor offsets
   float* d_gtc2 = nullptr;
   long long* d_tc2ofs = nullptr;
+  size_t gtc2_cap = 0, tc2ofs_cap = 0;   // floats, entries
   std::vector<long long> tc2_ofs;
   // autotuned right-hand sides per CTA of the 2D local solve, per nrhs, and the timings taken
   std::map<int, int> tuned_nr;
@@ -220,6 +223,10 @@ struct ddm_ctx {
   ddm::z64* d_gout = nullptr;
   struct GraphRec { int nrhs, K; cudaGraphExec_t exec; long long kernels; };
   std::vector<GraphRec> graphs;
+  void drop_graphs() {   // a buffer the captured kernels address was reallocated
+    for (auto& gr : graphs) cudaGraphExecDestroy(gr.exec);
+    graphs.clear();
+  }
   // kernels launched by this context (ddm_kernel_launches)
   long long nlaunch = 0;
   // timing

@@ -399,11 +399,24 @@ cudaError_t tc2d_pack_factors(ddm_ctx* c) {
     total += n;
     maxel = std::max(maxel, n);
   }
-  if (c->d_gtc2) { cudaFree(c->d_gtc2); c->d_gtc2 = nullptr; }
-  if (c->d_tc2ofs) { cudaFree(c->d_tc2ofs); c->d_tc2ofs = nullptr; }
+  // grow-only: a captured graph of M_K keeps addressing these buffers
+  if ((size_t)total > c->gtc2_cap) {
+    if (c->d_gtc2) cudaFree(c->d_gtc2);
+    c->d_gtc2 = nullptr;
+    c->gtc2_cap = 0;
+    c->drop_graphs();
+    if ((e = cudaMalloc((void**)&c->d_gtc2, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
+    c->gtc2_cap = (size_t)total;
+  }
+  if ((size_t)c->nfac > c->tc2ofs_cap) {
+    if (c->d_tc2ofs) cudaFree(c->d_tc2ofs);
+    c->d_tc2ofs = nullptr;
+    c->tc2ofs_cap = 0;
+    c->drop_graphs();
+    if ((e = cudaMalloc((void**)&c->d_tc2ofs, sizeof(long long) * c->nfac)) != cudaSuccess) return e;
+    c->tc2ofs_cap = (size_t)c->nfac;
+  }
   TC2Fac* d_facs = nullptr;
-  if ((e = cudaMalloc((void**)&c->d_gtc2, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
-  if ((e = cudaMalloc((void**)&c->d_tc2ofs, sizeof(long long) * c->nfac)) != cudaSuccess) return e;
   if ((e = cudaMalloc((void**)&d_facs, sizeof(TC2Fac) * c->nfac)) != cudaSuccess) return e;
   cudaMemcpyAsync(d_facs, facs.data(), sizeof(TC2Fac) * c->nfac, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->d_tc2ofs, c->tc2_ofs.data(), sizeof(long long) * c->nfac, cudaMemcpyHostToDevice, c->st);

@@ -281,8 +281,13 @@ cudaError_t tc3d_pack_factors(ddm_ctx* c) {
     c->tc_ofs[f] = total;
     total += tc3d_packed_floats(c->fac_b[f], c->fac_m[f]);
   }
-  if (c->d_gtc) { cudaFree(c->d_gtc); c->d_gtc = nullptr; }
-  if ((e = cudaMalloc((void**)&c->d_gtc, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
+  if ((size_t)total > c->gtc_cap) {
+    if (c->d_gtc) cudaFree(c->d_gtc);
+    c->d_gtc = nullptr;
+    c->gtc_cap = 0;
+    if ((e = cudaMalloc((void**)&c->d_gtc, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
+    c->gtc_cap = (size_t)total;
+  }
   for (int f = 0; f < c->nfac; ++f) {
     const int b = c->fac_b[f], m = c->fac_m[f];
     const int nIT = (b + TC3_TILE - 1) / TC3_TILE, nKC = (b + TC3_KC - 1) / TC3_KC;

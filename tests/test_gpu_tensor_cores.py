@@ -182,3 +182,25 @@ def test_rhs_per_cta_validation():
     D.ddm_set_rhs_per_cta(s.ctx, 4)
     D.ddm_set_rhs_per_cta(s.ctx, 0)
     s.close()
+
+
+def test_2d_graph_replay_survives_refactorisation():
+    """A graph of M_K captured before ddm_set_medium + ddm_factor keeps addressing valid factor
+    buffers: replays after a new medium give what a context without graphs gives."""
+    wl = W.tiny_2d(seed=27, n=32, parts=(2, 2), ov=2, npml=6, nrhs=16)
+    o = oracle_of(wl)
+    b = np.stack([o.rhs(wl.f[r]) for r in range(16)])
+    c2 = np.asarray(wl.c) * 1.1                       # a second medium
+    outs = {}
+    for graph in (True, False):
+        s = D.Solver(wl, precision=D.DDM_MIXED, max_rhs=16).factor()
+        D.ddm_set_rhs_per_cta(s.ctx, 64)                 # the same kernel in both contexts
+        D.ddm_set_graph(s.ctx, graph)
+        w = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+        D.ddm_apply(s.ctx, 3, s.to_dev(b), w, 16)       # captures the graph (first medium)
+        D.ddm_set_medium(s.ctx, wl.omega, s.to_dev(c2, torch.float64))
+        D.ddm_factor(s.ctx)
+        D.ddm_apply(s.ctx, 3, s.to_dev(b), w, 16)       # replays it on the second medium's factors
+        outs[graph] = w.cpu().numpy()
+        s.close()
+    assert rel(outs[True], outs[False]) < 1e-12

@@ -11,6 +11,9 @@
 #include <tuple>
 #include <vector>
 
+#include <mutex>
+#include <set>
+
 #include "ddm_internal.cuh"
 
 using namespace ddm;
@@ -1029,3 +1032,25 @@ extern "C" ddm_status ddm_factor_bytes(const ddm_ctx* c, int64_t* per_solve, int
   if (stored) *stored = c->fac_elems * el;
   return DDM_OK;
 }
+
+// ------------------------------------------------------------------------------------------
+namespace ddm {
+cudaError_t allow_dynamic_smem(const void* func, size_t need) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess) return e;
+  const size_t maxdyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  if (need > maxdyn) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({func, dev})) return cudaSuccess;
+  if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn)) != cudaSuccess)
+    return e;
+  done.insert({func, dev});
+  return cudaSuccess;
+}
+}  // namespace ddm

@@ -275,6 +275,12 @@ cudaError_t launch_lsq_update_b(ddm_ctx* c, int nb, const int* d_jr, int m, cons
                                 long long n);
 int ring_slots(const ddm_ctx* c);
 cudaError_t launch_factor3d(ddm_ctx* c, const std::vector<int>& reps);
+// Make `need` bytes of dynamic shared memory launchable for kernel `func` on the current
+// device.  The limit is process-wide state of the kernel, so it is raised once to everything the
+// device allows beside the kernel's static shared memory (under a lock) instead of being set to
+// each context's size before each launch, which races between host threads driving different
+// contexts.  cudaErrorInvalidValue if `need` exceeds what the device allows.
+cudaError_t allow_dynamic_smem(const void* func, size_t need);
 cudaError_t launch_local_solve3d(ddm_ctx* c, const void* src, void* out, void* U, int nrhs);
 long long tc3d_packed_floats(int b, int m);
 long long tc2d_packed_floats(int b, int m);

@@ -170,12 +170,12 @@ cudaError_t launch_factor_all(ddm_ctx* c, const int* d_reps, const long long* d_
   for (int f = 0; f < c->nfac; ++f) sm = std::max(sm, factor_smem_bytes(c->fac_b[f], c->fac_ldb[f], c->prec));
   cudaError_t e;
   if (c->prec == DDM_MIXED) {
-    e = cudaFuncSetAttribute(k_factor2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dynamic_smem((const void*)k_factor2d<float>, sm);
     if (e != cudaSuccess) return e;
     ++c->nlaunch;
     k_factor2d<float><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
   } else {
-    e = cudaFuncSetAttribute(k_factor2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = allow_dynamic_smem((const void*)k_factor2d<double>, sm);
     if (e != cudaSuccess) return e;
     ++c->nlaunch;
     k_factor2d<double><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (z64*)c->d_G, c->d_err);

@@ -14,6 +14,9 @@
 // written coalesced, so no global load sits on the sweep's critical path.  Waits are bounded:
 // on time-out the kernel records ERRBIT_TIMEOUT and runs to completion without hanging.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "ddm_internal.cuh"
 
@@ -266,7 +269,7 @@ static cudaError_t solve_nr(ddm_ctx* c, const void* src, void* out, void* U, int
   int nst = (int)std::min<size_t>(32, budget > fixed ? (budget - fixed) / stage : 0);
   nst = std::max(nst, 2);
   const size_t sm = fixed + (size_t)nst * stage;
-  cudaError_t e = cudaFuncSetAttribute(k_solve2d<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)k_solve2d<T, NR>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid(c->g.nsub, (nrhs + NR - 1) / NR);
   ++c->nlaunch;
@@ -288,11 +291,28 @@ static cudaError_t solve_with(ddm_ctx* c, int nr, const void* src, void* out, vo
   }
 }
 
-// Kernel and right-hand sides per CTA for nrhs right-hand sides: measured once per context and
-// nrhs by timing every candidate on the call's own source into a scratch output, then cached.
+// Kernel and right-hand sides per CTA for nrhs right-hand sides: measured once by timing every
+// candidate on the call's own source into a scratch output, then cached.
 // CUDA-core candidates: 1, 2, 4, 8 (8 only in complex64) right-hand sides per CTA -- more read
 // each factor block fewer times but raise the registers per thread, which can cut the CTAs per
 // SM.  Tensor-core candidate (complex64, packed factor, tensor cores enabled, nrhs >= 8): 64 per CTA.
+// Choices are also shared across contexts of the process, keyed by the subdomain geometry, the
+// precision, the tensor-core setting and nrhs: a later context with the same shapes (a served
+// request, say) reuses the choice instead of timing again, possibly under other contexts' load,
+// so the same shapes always run the same kernels (and give the same bits).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<unsigned long long, int, int>, int> g_tune;
+
+static unsigned long long geometry_key(const ddm_ctx* c) {
+  unsigned long long h = 0x9E3779B97F4A7C15ull ^ (unsigned long long)c->dim ^ ((unsigned long long)c->prec << 8);
+  auto mix = [&](unsigned long long v) {
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+  };
+  mix((unsigned long long)c->g.nsub);
+  for (const auto& s : c->subs) mix(((unsigned long long)s.ext[0] << 40) ^ ((unsigned long long)s.ext[1] << 20) ^ s.ext[2]);
+  return h;
+}
+
 template <typename T>
 static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int nrhs) {
   if (nrhs == 1) return solve_nr<T, 1>(c, src, out, U, 1);
@@ -300,6 +320,12 @@ static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int 
   if (c->forced_nr > 0 && (c->forced_nr <= 8 || tc)) return solve_with<T>(c, c->forced_nr, src, out, U, nrhs);
   const int key = tc ? nrhs : -nrhs;   // cached choices with and without the tensor cores
   auto it = c->tuned_nr.find(key);
+  const auto gkey = std::make_tuple(geometry_key(c), key, (int)sizeof(T));
+  if (it == c->tuned_nr.end()) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto g = g_tune.find(gkey);
+    if (g != g_tune.end()) it = c->tuned_nr.emplace(key, g->second).first;
+  }
   if (it == c->tuned_nr.end()) {
     // scratch output and accumulator: the candidates are timed with the accumulation the DDM
     // steps ask for
@@ -331,7 +357,10 @@ static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int 
     cudaEventDestroy(e1);
     cudaFree(scratch);
     if (e != cudaSuccess) return e;
-    it = c->tuned_nr.emplace(key, best).first;
+    // a context that tuned the same shapes at the same time may have been first: use its choice
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int chosen = g_tune.emplace(gkey, best).first->second;
+    it = c->tuned_nr.emplace(key, chosen).first;
   }
   return solve_with<T>(c, it->second, src, out, U, nrhs);
 }

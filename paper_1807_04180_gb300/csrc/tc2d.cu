@@ -453,7 +453,7 @@ cudaError_t tc2d_solve(ddm_ctx* c, int nrt, const void* src, void* out, void* U,
   int nst = 0;
   const size_t sm = tc2d_smem(c, &nst);
   if (!sm) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_solve2d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = allow_dynamic_smem((const void*)k_solve2d_tc, sm);
   if (e != cudaSuccess) return e;
   dim3 grid((nrhs + TC2_NRT - 1) / TC2_NRT, c->g.nsub);
   ++c->nlaunch;

@@ -301,7 +301,7 @@ cudaError_t tc3d_pack_factors(ddm_ctx* c) {
 // all plane steps of the forward and backward sweeps of one factor group
 cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, const c32* cS, const c32* cN,
                         const c32* src, c32* out, c32* U) {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC3_SMEM);
+  cudaError_t e = allow_dynamic_smem((const void*)k_gemm3d_tc, TC3_SMEM);
   if (e != cudaSuccess) return e;
   const int b = c->fac_b[f], m = c->fac_m[f];
   const int nIT = (b + TC3_TILE - 1) / TC3_TILE, nKC = (b + TC3_KC - 1) / TC3_KC;

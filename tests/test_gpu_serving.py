@@ -30,7 +30,7 @@ def test_results_same_alone_and_in_the_mix():
     assert mix.wait(ids, timeout=300)
     st = mix.stats()
     mix.shutdown()
-    assert st["completed"] == 4 and st["failed"] == 0
+    assert st["completed"] == 4 and st["failed"] == 0, [mix.poll(i).error for i in ids]
     for i, r in zip(ids, ref):
         got = mix.poll(i)
         assert got.info["converged"] and got.info["rel_residual"] <= 1e-8

@@ -281,21 +281,33 @@ def solve_traffic(precision):
 
 
 def profile_kernels(args):
-    """Small profiling case on the bench workload: medium assembly, factorisation and one
-    preconditioner application with K = 4 (4 batched local solves, 3 transfers), repeated
-    warmup + steps times.  Holds about 1.5 GB on the device."""
+    """Small profiling cases (a few GB on the device), repeated warmup + steps times:
+    - heterogeneous_2d: the bench workload's medium assembly, factorisation and one
+      preconditioner application with K = 4 (4 batched local solves, 3 transfers); ~1.5 GB;
+    - layered_2d_batched: the same layered recipe on 512^2 with 8 x 8 uneven subdomains and 64
+      point sources, tensor-core local solves (64 right-hand sides per CTA), K = 2; ~2 GB;
+    - constant_3d: the 3D constant medium on 144^3 with 6 x 6 x 6 subdomains of 24^3 (the bench
+      workload's subdomain and shared factor, 216 columns), K = 2; ~2.5 GB."""
     import torch
     from paper_1807_04180_gb300 import ddm as D
-    wl = W.heterogeneous_2d()
-    prec = D.DDM_MIXED if args.precision == "mixed" else D.DDM_FP64
-    s = D.Solver(wl, precision=prec, max_rhs=1)
-    b = torch.zeros(wl.c.shape, dtype=torch.complex128, device="cuda")
-    D.ddm_rhs(s.ctx, s.to_dev(wl.f[0]), b)
+    if args.workload == "heterogeneous_2d":
+        wl, K, nrhs = W.heterogeneous_2d(), 4, 1
+        prec = D.DDM_MIXED if args.precision == "mixed" else D.DDM_FP64
+    elif args.workload == "layered_2d_batched":
+        wl, K, nrhs, prec = W.layered_2d_batched(n=512, parts=8, nrhs=64), 2, 64, D.DDM_MIXED
+    else:
+        wl, K, nrhs, prec = W.constant_3d(n=144, parts=6), 2, 1, D.DDM_MIXED
+    s = D.Solver(wl, precision=prec, max_rhs=nrhs)
+    if nrhs >= 16:
+        D.ddm_factor(s.ctx)
+        D.ddm_set_rhs_per_cta(s.ctx, 64)
+    b = torch.zeros((nrhs,) + wl.c.shape, dtype=torch.complex128, device="cuda")
+    D.ddm_rhs(s.ctx, s.to_dev(np.ascontiguousarray(wl.f[:nrhs])), b, nrhs)
     w = torch.zeros_like(b)
     for _ in range(args.warmup + args.steps):
         D.ddm_set_medium(s.ctx, wl.omega, s.c)
         D.ddm_factor(s.ctx)
-        D.ddm_apply(s.ctx, 4, b, w)
+        D.ddm_apply(s.ctx, K, b, w, nrhs)
     torch.cuda.synchronize()
     s.close()
 

@@ -5,16 +5,19 @@
 // off-diagonal blocks L_k = diag(c_S(., k)), U_k = diag(c_N(., k)).  Block elimination
 // gives D_0 = T_0, D_k = T_k - L_k D_{k-1}^{-1} U_{k-1}; the factor stores
 // G_k = D_k^{-1} (dense b x b, column-major, leading dimension ldb), inverted in shared memory
-// by Gauss-Jordan elimination with partial (row) pivoting inside the block.  One CTA per
-// distinct factor walks the lines sequentially.
+// by blocked Gauss-Jordan elimination with partial (row) pivoting inside the block.  One CTA
+// per distinct factor walks the lines sequentially.
 #include <algorithm>
 
 #include "ddm_internal.cuh"
 
 namespace ddm {
 
+constexpr int FAC_W = 4;          // panel width of the blocked Gauss-Jordan inversion
+constexpr int FAC_THREADS = 256;  // per CTA: two CTAs per SM in complex64 (registers, shared memory)
+
 template <typename T>
-__global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const long long* fofs_arr,
+__global__ void __launch_bounds__(FAC_THREADS, sizeof(T) == 4 ? 2 : 1) k_factor2d(Geom g, const int* reps, const long long* fofs_arr,
                                                   const int* ldbs, cplx<T>* Gout, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SubDesc& s = g.subs[reps[blockIdx.x]];
@@ -24,8 +27,8 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
   const int njj = (b + 31) / 32;             // 32-column groups per row
   const int ldm = 32 * njj + 1;              // padded, odd: whole lane groups, conflict-free columns
   cplx<T>* M = (cplx<T>*)smem;               // b x ldm working block
-  cplx<T>* colp = M + (long long)b * ldm;    // column p multipliers
-  cplx<T>* cC = colp + b;                    // centre of line k
+  cplx<T>* Tp = M + (long long)b * ldm;      // FAC_W x ldm: old pivot rows of a panel
+  cplx<T>* cC = Tp + (long long)FAC_W * ldm; // centre of line k
   cplx<T>* cE = cC + b;                      // x+ coupling
   cplx<T>* cW = cE + b;                      // x- coupling
   cplx<T>* cS = cW + b;                      // coupling of line k to line k-1
@@ -33,8 +36,7 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
   cplx<T>* cNn = cNp + b;
   int* perm = (int*)(cNn + b);
   int* cm = perm + b;
-  __shared__ int s_piv, s_bad;
-  __shared__ cplx<T> s_inv, s_app;
+  __shared__ int s_bad;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   if (tid == 0) s_bad = 0;
@@ -78,65 +80,137 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
     __syncthreads();
     for (int j = tid; j < b; j += nth) cNp[j] = cNn[j];   // read by the next line's build only
 
-    // Gauss-Jordan inversion with partial pivoting, in place
-    for (int p = 0; p < b; ++p) {
+    // Gauss-Jordan inversion with partial pivoting, in place, blocked by panels of FAC_W
+    // columns.  For a panel P = [p0, p0 + w): warp 0 runs the unblocked elimination on the
+    // panel's columns only (pivot search over rows >= c, interchange, scaling, elimination of
+    // column c from every other row), which leaves the panel holding the new column block
+    // [-A_01 A_11^-1 ; A_11^-1 ; -A_21 A_11^-1] of the inverse.  The interchanges are then
+    // applied to the other columns, the old pivot rows T = rows P (other columns) are kept, and
+    // every other column j takes the same w elimination steps at once:
+    //   rows i outside P:  M[i][j] += sum_q M[i][p0+q] T[q][j]
+    //   rows of P:         M[p0+q'][j] = sum_q M[p0+q'][p0+q] T[q][j]
+    // (the block Gauss-Jordan step; three barriers per panel instead of three per pivot)
+    for (int p0 = 0; p0 < b; p0 += FAC_W) {
+      const int w = min(FAC_W, b - p0);
       if (warp == 0) {
-        T best = (T)-1; int bi = p;
-        for (int i = p + lane; i < b; i += 32) {
-          T a = cabs2(M[i * ldm + p]);
-          if (a > best) { best = a; bi = i; }
+        // the panel in registers: R[t][q] = M[lane + 32 t][p0 + q]
+        cplx<T> R[4][FAC_W];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int q = 0; q < FAC_W; ++q) {
+            const int i = lane + 32 * t;
+            R[t][q] = (i < b && q < w) ? M[i * ldm + p0 + q] : mk<T>(0, 0);
+          }
+#pragma unroll
+        for (int qc = 0; qc < FAC_W; ++qc) {
+          if (qc >= w) break;
+          const int c = p0 + qc;
+          // pivot: largest |M[i][c]| over rows i >= c (ties to the lowest row)
+          T best = (T)-1; int bi = c;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i >= c && i < b) {
+              const T a = cabs2(R[t][qc]);
+              if (a > best) { best = a; bi = i; }
+            }
+          }
+          for (int o = 16; o; o >>= 1) {
+            const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          if (lane == 0) {
+            perm[c] = bi;
+            if (!(best > (T)0) || !isfinite(best)) s_bad = 1;
+          }
+          // rows c and bi as every lane sees them: row c's and row bi's panel values
+          const int lc = c & 31, tcr = c >> 5, lr = bi & 31, trr = bi >> 5;
+          cplx<T> vc[FAC_W], vr[FAC_W];
+#pragma unroll
+          for (int q = 0; q < FAC_W; ++q) {
+            cplx<T> sc = R[0][q], sr = R[0][q];
+#pragma unroll
+            for (int t = 1; t < 4; ++t) {
+              if (tcr == t) sc = R[t][q];
+              if (trr == t) sr = R[t][q];
+            }
+            vc[q].x = __shfl_sync(0xffffffffu, sc.x, lc);
+            vc[q].y = __shfl_sync(0xffffffffu, sc.y, lc);
+            vr[q].x = __shfl_sync(0xffffffffu, sr.x, lr);
+            vr[q].y = __shfl_sync(0xffffffffu, sr.y, lr);
+          }
+          // the interchange: row bi takes row c's values (the pivot row is written below)
+          if (bi != c && lane == lr) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (trr == t)
+#pragma unroll
+                for (int q = 0; q < FAC_W; ++q) R[t][q] = vc[q];
+          }
+          // pivot row after the interchange, scaled; column c of the inverse
+          const cplx<T> pv = vr[qc];
+          const cplx<T> inv = (best > (T)0 && isfinite(best)) ? cinv(pv) : mk<T>(0, 0);
+          cplx<T> rs[FAC_W];
+#pragma unroll
+          for (int q = 0; q < FAC_W; ++q) rs[q] = q == qc ? inv : vr[q] * inv;
+          // eliminate column c from the other rows; the pivot row becomes rs
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i == c) {
+#pragma unroll
+              for (int q = 0; q < FAC_W; ++q) R[t][q] = rs[q];
+            } else {
+              const cplx<T> fi = -R[t][qc];
+#pragma unroll
+              for (int q = 0; q < FAC_W; ++q) {
+                if (q == qc) R[t][q] = fi * inv;
+                else cfma(R[t][q], fi, rs[q]);
+              }
+            }
+          }
         }
-        for (int o = 16; o; o >>= 1) {
-          T ob = __shfl_xor_sync(0xffffffffu, best, o);
-          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (lane == 0) {
-          s_piv = bi;
-          s_app = M[p * ldm + p];
-          cplx<T> pv = M[bi * ldm + p];
-          if (!(best > (T)0) || !isfinite(best)) { s_bad = 1; s_inv = mk<T>(0, 0); }
-          else s_inv = cinv(pv);
-          perm[p] = bi;
-        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int q = 0; q < FAC_W; ++q) {
+            const int i = lane + 32 * t;
+            if (i < b && q < w) M[i * ldm + p0 + q] = R[t][q];
+          }
       }
       __syncthreads();
-      const int r = s_piv;
-      const cplx<T> inv = s_inv;
-      // interchange rows p and r, scale the pivot row, keep the multipliers of column p and
-      // clear column p in the other rows (their final entry there, -f_i / pivot, comes out of
-      // the update below).  Thread j alone reads and writes M[p][j], M[r][j] and M[j][p]; the
-      // old M[p][p], needed as row r's multiplier, was saved by the pivot search.
-      if (tid < b) {
-        const int j = tid;
-        const cplx<T> ap = M[p * ldm + j];
-        const cplx<T> ar = M[r * ldm + j];
-        colp[j] = (j == p) ? mk<T>(0, 0) : (j == r ? s_app : M[j * ldm + p]);
-        M[p * ldm + j] = (j == p) ? inv : ar * inv;
-        if (r != p) M[r * ldm + j] = (j == p) ? mk<T>(0, 0) : ap;
-        if (j != p && j != r) M[j * ldm + p] = mk<T>(0, 0);
+      // the panel's interchanges on the other columns, in order, and the old pivot rows
+      for (int j = tid; j < b; j += nth) {
+        if (j >= p0 && j < p0 + w) continue;
+        for (int c = p0; c < p0 + w; ++c) {
+          const int r = perm[c];
+          if (r != c) {
+            const cplx<T> t0 = M[c * ldm + j];
+            M[c * ldm + j] = M[r * ldm + j];
+            M[r * ldm + j] = t0;
+          }
+        }
+        for (int q = 0; q < w; ++q) Tp[q * ldm + j] = M[(p0 + q) * ldm + j];
       }
       __syncthreads();
-      // eliminate column p from every other row (warp per row set, lanes over columns, the
-      // pivot row in registers, zero in the padding columns so those stay inert)
-      {
-        cplx<T> mp[4];
+      // rank-w update of the other columns: warp per row set, lanes over columns (the pivot
+      // rows' old values read from Tp, conflict-free along the lanes)
+      for (int i = warp; i < b; i += nwarp) {
+        const bool prow = i >= p0 && i < p0 + w;
+        cplx<T> mi[FAC_W];
+#pragma unroll
+        for (int q = 0; q < FAC_W; ++q) mi[q] = q < w ? M[i * ldm + p0 + q] : mk<T>(0, 0);
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-          int j = lane + 32 * jj;
-          mp[jj] = j < b ? M[p * ldm + j] : mk<T>(0, 0);
-        }
-        for (int i = warp; i < b; i += nwarp) {
-          if (i == p) continue;
-          const cplx<T> f = -colp[i];
-          cplx<T>* Mi = M + i * ldm + lane;
+          const int j = lane + 32 * jj;
+          if (jj < njj && j < b && (j < p0 || j >= p0 + w)) {
+            cplx<T> acc = prow ? mk<T>(0, 0) : M[i * ldm + j];
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            if (jj < njj) {
-              cplx<T> cur = Mi[32 * jj];
-              cfma(cur, f, mp[jj]);
-              Mi[32 * jj] = cur;
-            }
+            for (int q = 0; q < FAC_W; ++q)
+              if (q < w) cfma(acc, mi[q], Tp[q * ldm + j]);
+            M[i * ldm + j] = acc;
           }
         }
       }
@@ -160,7 +234,7 @@ __global__ void __launch_bounds__(512) k_factor2d(Geom g, const int* reps, const
 size_t factor_smem_bytes(int b, int ldb, int prec) {
   size_t el = prec == DDM_MIXED ? sizeof(c32) : sizeof(z64);
   (void)ldb;
-  return (size_t)b * (32 * ((b + 31) / 32) + 1) * el + 7 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
+  return (size_t)(b + FAC_W) * (32 * ((b + 31) / 32) + 1) * el + 6 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
 }
 
 // All distinct factors in one launch, one CTA each.  d_reps[f] is a subdomain using factor
@@ -173,12 +247,12 @@ cudaError_t launch_factor_all(ddm_ctx* c, const int* d_reps, const long long* d_
     e = allow_dynamic_smem((const void*)k_factor2d<float>, sm);
     if (e != cudaSuccess) return e;
     ++c->nlaunch;
-    k_factor2d<float><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
+    k_factor2d<float><<<c->nfac, FAC_THREADS, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
   } else {
     e = allow_dynamic_smem((const void*)k_factor2d<double>, sm);
     if (e != cudaSuccess) return e;
     ++c->nlaunch;
-    k_factor2d<double><<<c->nfac, 512, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (z64*)c->d_G, c->d_err);
+    k_factor2d<double><<<c->nfac, FAC_THREADS, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (z64*)c->d_G, c->d_err);
   }
   return cudaGetLastError();
 }

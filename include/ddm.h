@@ -32,6 +32,9 @@
  *   - "Local vectors" (debug/parity entry points only) concatenate every
  *     subdomain's extended grid (x fastest), subdomains in C order of their
  *     index (z slowest, x fastest); ddm_local_layout() gives the offsets.
+ *     With nrhs right-hand sides they are subdomain-major: subdomain s's
+ *     nrhs vectors are adjacent, right-hand side r at element
+ *     offsets[s] * nrhs + r * (ext_x[s] * ext_y[s] * ext_z[s]).
  *
  * Conventions for every entry point
  *   - Returns a ddm_status; never aborts or exits.  On error the context keeps
@@ -214,15 +217,18 @@ ddm_status ddm_global_apply(ddm_ctx *ctx, const void *x_dev, void *y_dev, int nr
 ddm_status ddm_residual(ddm_ctx *ctx, const void *b_dev, const void *x_dev, void *r_dev, int nrhs,
                         double *norms_host);
 
-/* Local layout: number of subdomains, total local length, and (optional,
- * host arrays of n_sub entries) each subdomain's element offset and its
- * extended size along x, y, z.                                              */
+/* Local layout: number of subdomains, total local length (one right-hand
+ * side), and (optional, host arrays of n_sub entries) each subdomain's
+ * element offset for one right-hand side and its extended size along x, y,
+ * z.  With nrhs right-hand sides, right-hand side r of subdomain s starts at
+ * offsets[s] * nrhs + r * ext_x[s] * ext_y[s] * ext_z[s].                   */
 ddm_status ddm_local_layout(const ddm_ctx *ctx, int *n_sub, int64_t *total, int64_t *offsets,
                             int *ext_x, int *ext_y, int *ext_z);
 
 /* u_R = L^_R^{-1} src_R for every subdomain R (the batched local solves of
- * Eqs. (talg_1)/(talg_2)); local complex vectors, device, in the context's
- * local precision (complex128 for DDM_FP64, complex64 for DDM_MIXED).      */
+ * Eqs. (talg_1)/(talg_2)); local complex vectors (total * nrhs elements,
+ * subdomain-major as above), device, in the context's local precision
+ * (complex128 for DDM_FP64, complex64 for DDM_MIXED).                       */
 ddm_status ddm_local_solve(ddm_ctx *ctx, const void *src_dev, void *u_dev, int nrhs);
 
 /* Run `nsteps` steps of Algorithm 3.1 from the global right-hand side b_dev

@@ -177,7 +177,7 @@ cudaError_t launch_factor3d(ddm_ctx* c, const std::vector<int>& reps) {
 //                      out_q[k b + i] = C[i][q]; at k = m-1 also U_q += C
 //   backward (pass 1): C = G_k Z,  Z[j][q] = c_zp(j,k) out_q[(k+1) b + j]
 //                      x = out_q[k b + i] - C[i][q]; out_q = x; U_q += x
-// colofs[q] = element offset of column q's local vector (subdomain offset + rhs * ltotal).
+// colofs[q] = element offset of column q's local vector (lvofs of its subdomain and rhs).
 constexpr int G3_BM = 64, G3_BN = 64, G3_BK = 16;
 
 template <typename T>
@@ -256,9 +256,10 @@ static cudaError_t solve3d_t(ddm_ctx* c, const void* src, void* out, void* U, in
   // columns grouped by factor
   std::vector<std::vector<long long>> cols(c->nfac);
   std::vector<int> rep(c->nfac, -1);
-  for (int r = 0; r < nrhs; ++r)
-    for (int s = 0; s < c->g.nsub; ++s) {
-      cols[c->subs[s].fid].push_back(c->subs[s].vofs + (long long)r * c->g.ltotal);
+  // a subdomain's right-hand sides in adjacent columns (and adjacent in memory)
+  for (int s = 0; s < c->g.nsub; ++s)
+    for (int r = 0; r < nrhs; ++r) {
+      cols[c->subs[s].fid].push_back(lvofs(c->subs[s], r, nrhs));
       if (rep[c->subs[s].fid] < 0) rep[c->subs[s].fid] = s;
     }
   cudaError_t e = cudaSuccess;

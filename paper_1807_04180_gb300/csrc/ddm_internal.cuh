@@ -55,6 +55,9 @@ typedef cplx<float> c32;    // complex64
 constexpr int MAXDIM = 3;
 constexpr int NDIR = 27;     // direction code (dx+1) + 3 (dy+1) + 9 (dz+1); 13 = centre
 
+struct SubDesc;
+__host__ __device__ inline long long lvofs(const SubDesc& s, int r, int nrhs);
+
 struct SubDesc {
   int idx[MAXDIM];     // part index per physical axis
   int lo[MAXDIM];      // own node start (global interior node index)
@@ -67,10 +70,19 @@ struct SubDesc {
   int pad;            // leading dimension of its factor blocks
   int sofs, scnt;      // its range in the strip-node list (nodes that receive a transfer)
   int pad2;
-  long long vofs;      // offset of its local vector
+  long long vofs;      // offset of its local vector with one right-hand side (see lvofs)
   long long fofs;      // element offset of its factor (blocks of b x ldb)
   int nbr[NDIR];       // neighbour id per direction code, -1 if none (nbr[13] = self)
 };
+
+// Element offset of right-hand side r's local vector of subdomain s when nrhs right-hand sides
+// are stored: subdomain-major, i.e. the nrhs vectors of subdomain 0, then those of subdomain 1,
+// ...  A CTA that works on one subdomain and many right-hand sides then touches one contiguous
+// region instead of nrhs regions ltotal elements apart (far fewer pages and DRAM rows).
+__host__ __device__ inline long long lvofs(const SubDesc& s, int r, int nrhs) {
+  return s.vofs * nrhs + (long long)r * s.ext[0] * s.ext[1] * s.ext[2];
+}
+
 
 // everything a kernel needs to evaluate the operator and the partition
 struct Geom {

@@ -128,11 +128,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve2d(Geom g, const cplx<T>
   // side, prefetch); both halves accumulate the GEMV over their half of each chunk.
   const int row = tid & 127, half = tid >> 7;
   const bool owner = half == 0 && row < b;
-  const long long lt = g.ltotal;
   const long long len = (long long)b * m;
-  const cplx<T>* srcv = src + (long long)r0 * lt + s.vofs;
-  cplx<T>* outv = out + (long long)r0 * lt + s.vofs;
-  cplx<T>* Uv = U ? U + (long long)r0 * lt + s.vofs : nullptr;
+  const long long lt = len;   // right-hand sides of one subdomain are adjacent (lvofs)
+  const cplx<T>* srcv = src + lvofs(s, r0, nrhs);
+  cplx<T>* outv = out + lvofs(s, r0, nrhs);
+  cplx<T>* Uv = U ? U + lvofs(s, r0, nrhs) : nullptr;
   const cplx<T>* lc = (const cplx<T>*)g.lcoef + s.vofs * 5;      // planes: C, W, E, S, N
   const cplx<T>* cSp = lc + 3 * len;
   const cplx<T>* cNp = lc + 4 * len;

@@ -46,7 +46,7 @@ __global__ void k_restrict(Geom g, const z64* b, cplx<T>* src, cplx<T>* U) {
   unflat(i, s.ext, x);
   cplx<T> v = mk<T>(0, 0);
   if (in_own(g, s, x)) v = ccast<T>(b[(long long)r * g.nglob + gflat(g, s, x)]);
-  long long o = (long long)r * g.ltotal + s.vofs + i;
+  long long o = lvofs(s, r, (int)gridDim.z) + i;
   src[o] = v;
   if (U) U[o] = mk<T>(0, 0);
 }
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>
         if (!want_res && k != lagd - 1) continue;
         const int sl = ring.res_slot[k];
         if (sl < 0) continue;
-        const cplx<T>* u = (const cplx<T>*)ring.p[sl] + (long long)r * g.ltotal + S.vofs;
+        const cplx<T>* u = (const cplx<T>*)ring.p[sl] + lvofs(S, r, (int)gridDim.z);
         // -(A_R (beta_d u_S))(x)
         cplx<T> acc = mk<T>(0, 0);
         {
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>
         acc_res = acc_res - acc;
       }
     }
-    src_next[(long long)r * g.ltotal + R.vofs + li] = acc_src;
+    src_next[lvofs(R, r, (int)gridDim.z) + li] = acc_src;
     if (want_res && (mask & 0x80000000u)) res2 = (double)acc_res.x * acc_res.x + (double)acc_res.y * acc_res.y;
   }
   if (want_res) {
@@ -261,7 +261,7 @@ __global__ void k_assemble(Geom g, const cplx<T>* U, z64* w, int nrhs) {
           int sid = (part[2] * g.parts[1] + part[1]) * g.parts[0] + part[0];
           const SubDesc& s = g.subs[sid];
           int xl[3] = {xg[0] - s.lo[0], xg[1] - s.lo[1], g.dim == 3 ? xg[2] - s.lo[2] : 0};
-          cplx<T> v = U[(long long)r * g.ltotal + s.vofs + flat(xl, s.ext)];
+          cplx<T> v = U[lvofs(s, r, nrhs) + flat(xl, s.ext)];
           double bw = wt[0][i0] * wt[1][i1] * wt[2][i2];
           acc = acc + bw * mk<double>((double)v.x, (double)v.y);
         }

@@ -23,6 +23,23 @@ def from_local(o, flat):
     return out
 
 
+def to_local_batch(o, per_rhs, dtype=np.complex128):
+    """Local vectors of several right-hand sides (a list of per-subdomain dicts) in the library's
+    multi-right-hand-side layout: subdomain-major, the vectors of one subdomain adjacent."""
+    return np.concatenate([np.asarray(sr[R], dtype=dtype).ravel() for R in o.subs for sr in per_rhs])
+
+
+def from_local_batch(o, flat, nrhs):
+    """Inverse of to_local_batch: a list of nrhs per-subdomain dicts."""
+    out, ofs = [dict() for _ in range(nrhs)], 0
+    for R in o.subs:
+        n = int(np.prod(o.sub_shape[R]))
+        for r in range(nrhs):
+            out[r][R] = np.asarray(flat[ofs: ofs + n]).reshape(o.sub_shape[R])
+            ofs += n
+    return out
+
+
 def rel(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()

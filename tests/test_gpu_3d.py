@@ -8,7 +8,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from gpu_helpers import from_local, oracle_of, rel, to_local  # noqa: E402
+from gpu_helpers import from_local, from_local_batch, oracle_of, rel, to_local, to_local_batch  # noqa: E402
 from paper_1807_04180_gb300 import ddm as D  # noqa: E402
 from paper_1807_04180_gb300 import workloads as W  # noqa: E402
 
@@ -51,13 +51,13 @@ def test_3d_local_solves(name, prec):
     srcs = [{R: cplx(rng, o.sub_shape[R]) for R in o.subs} for _ in range(2)]
     dt = np.complex128 if prec == D.DDM_FP64 else np.complex64
     tdt = torch.complex128 if prec == D.DDM_FP64 else torch.complex64
-    src = np.concatenate([to_local(o, sr, dt) for sr in srcs])
+    src = to_local_batch(o, srcs, dt)
     u = torch.zeros(src.shape, dtype=tdt, device="cuda")
     D.ddm_local_solve(s.ctx, s.to_dev(src), u, 2)
-    u = u.cpu().numpy().reshape(2, -1)
+    gots = from_local_batch(o, u.cpu().numpy(), 2)
     tol = 1e-10 if prec == D.DDM_FP64 else 2e-4
     for r in range(2):
-        got = from_local(o, u[r])
+        got = gots[r]
         for R in o.subs:
             assert rel(got[R], o.local_solve(R, srcs[r][R])) < tol, (R, r)
     s.close()

@@ -14,7 +14,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from gpu_helpers import from_local, oracle_of, rel, to_local  # noqa: E402
+from gpu_helpers import from_local, from_local_batch, oracle_of, rel, to_local, to_local_batch  # noqa: E402
 from oracle.krylov import ddm_fgmres  # noqa: E402
 from paper_1807_04180_gb300 import ddm as D  # noqa: E402
 from paper_1807_04180_gb300 import workloads as W  # noqa: E402
@@ -74,13 +74,13 @@ def test_local_solves(name, prec):
     srcs = [{R: cplx(rng, o.sub_shape[R]) for R in o.subs} for _ in range(nrhs)]
     dt = np.complex128 if prec == D.DDM_FP64 else np.complex64
     tdt = torch.complex128 if prec == D.DDM_FP64 else torch.complex64
-    src = np.concatenate([to_local(o, sr, dt) for sr in srcs])
+    src = to_local_batch(o, srcs, dt)
     u = torch.zeros(src.shape, dtype=tdt, device=DEV)
     D.ddm_local_solve(s.ctx, s.to_dev(src), u, nrhs)
-    u = u.cpu().numpy().reshape(nrhs, -1)
+    gots = from_local_batch(o, u.cpu().numpy(), nrhs)
     tol = 1e-10 if prec == D.DDM_FP64 else 2e-4
     for r in range(nrhs):
-        got = from_local(o, u[r])
+        got = gots[r]
         for R in o.subs:
             assert rel(got[R], o.local_solve(R, srcs[r][R])) < tol, (R, r)
     s.close()

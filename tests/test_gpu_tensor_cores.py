@@ -7,7 +7,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from gpu_helpers import from_local, oracle_of, rel, to_local  # noqa: E402
+from gpu_helpers import from_local, from_local_batch, oracle_of, rel, to_local, to_local_batch  # noqa: E402
 from paper_1807_04180_gb300 import ddm as D  # noqa: E402
 from paper_1807_04180_gb300 import workloads as W  # noqa: E402
 
@@ -42,10 +42,11 @@ def _local_solves(wl, nrhs, tc):
     D.ddm_set_tensor_cores(s.ctx, tc)
     rng = np.random.default_rng(5)
     srcs = [{R: cplx(rng, o.sub_shape[R]) for R in o.subs} for _ in range(nrhs)]
-    src = np.concatenate([to_local(o, sr, np.complex64) for sr in srcs])
+    src = to_local_batch(o, srcs, np.complex64)
     u = torch.zeros(src.shape, dtype=torch.complex64, device="cuda")
     D.ddm_local_solve(s.ctx, s.to_dev(src), u, nrhs)
-    out = u.cpu().numpy().reshape(nrhs, -1)
+    # one row per right-hand side, each in the one-right-hand-side layout
+    out = np.stack([to_local(o, d, np.complex64) for d in from_local_batch(o, u.cpu().numpy(), nrhs)])
     s.close()
     return o, srcs, out
 
@@ -109,10 +110,11 @@ def _local2d(wl, nrhs, nr, seed=7):
     D.ddm_set_rhs_per_cta(s.ctx, nr)
     rng = np.random.default_rng(seed)
     srcs = [{R: cplx(rng, o.sub_shape[R]) for R in o.subs} for _ in range(nrhs)]
-    src = np.concatenate([to_local(o, sr, np.complex64) for sr in srcs])
+    src = to_local_batch(o, srcs, np.complex64)
     u = torch.zeros(src.shape, dtype=torch.complex64, device="cuda")
     D.ddm_local_solve(s.ctx, s.to_dev(src), u, nrhs)
-    out = u.cpu().numpy().reshape(nrhs, -1)
+    # one row per right-hand side, each in the one-right-hand-side layout
+    out = np.stack([to_local(o, d, np.complex64) for d in from_local_batch(o, u.cpu().numpy(), nrhs)])
     s.close()
     return o, srcs, out
 

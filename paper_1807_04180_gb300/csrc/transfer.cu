@@ -83,17 +83,26 @@ struct RingPtrs { const void* p[3]; int res_slot[3]; };
 template <typename T>
 struct CoefT { cplx<T> c, m[3], p[3]; };
 
+// Each thread takes one strip node of R and TR_RG right-hand sides (blockIdx.z = group): the
+// stencil terms of -A_R (beta_d .) at the node (sender index, coefficient x cut-off) are built
+// once per direction and applied to every right-hand side of the group.
+constexpr int TR_RG = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res) {
+__global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res,
+                                                  int nrhs) {
   const int Rid = blockIdx.y;
   const SubDesc& R = g.subs[Rid];
-  const int r = blockIdx.z;
+  const int r0 = blockIdx.z * TR_RG, nr = min(TR_RG, nrhs - r0);
   const int e = g.e, ov = g.ov, dim = g.dim;
   __shared__ T beta_s[32];
+  __shared__ double sh[TR_RG][4];
   if (threadIdx.x <= ov && threadIdx.x < 32) beta_s[threadIdx.x] = (T)g.beta[threadIdx.x];
   __syncthreads();
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
-  double res2 = 0.0;
+  double res2[TR_RG];
+#pragma unroll
+  for (int rr = 0; rr < TR_RG; ++rr) res2[rr] = 0.0;
   if (it < R.scnt) {
     const int li = g.sidx[R.sofs + it];
     const unsigned mask = g.smask[R.sofs + it];
@@ -107,7 +116,9 @@ __global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>
       cf.c = lc[0];
       for (int a = 0; a < dim; ++a) { cf.m[a] = lc[(1 + 2 * a) * len]; cf.p[a] = lc[(2 + 2 * a) * len]; }
     }
-    cplx<T> acc_src = mk<T>(0, 0), acc_res = mk<T>(0, 0);
+    cplx<T> acc_src[TR_RG], acc_res[TR_RG];
+#pragma unroll
+    for (int rr = 0; rr < TR_RG; ++rr) acc_src[rr] = acc_res[rr] = mk<T>(0, 0);
     unsigned dm = mask & 0x07ffffffu;
     while (dm) {
       const int code = __ffs(dm) - 1;
@@ -134,54 +145,83 @@ __global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>
           inside[a][o + 1] = in;
         }
       }
+      // terms t = 0 (centre) and 1 + 2 a + (o > 0) (neighbour along axis a): S-local index and
+      // coefficient x cut-off; `live` marks the terms that contribute
+      int tix[7];
+      cplx<T> tcf[7];
+      unsigned live = 0;
+      {
+        const T w0 = bw[0][1] * bw[1][1] * bw[2][1];
+        tix[0] = flat(y0, S.ext);
+        tcf[0] = mk<T>(w0 * cf.c.x, w0 * cf.c.y);
+        if (w0 != (T)0 && inside[0][1] && inside[1][1] && inside[2][1]) live |= 1u;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int oi = 0; oi < 2; ++oi) {
+          const int o = oi ? 1 : -1, t = 1 + 2 * a + oi;
+          tix[t] = 0;
+          tcf[t] = mk<T>(0, 0);
+          if (a >= dim) continue;
+          if ((o > 0 && x[a] + 1 >= R.ext[a]) || (o < 0 && x[a] == 0)) continue;   // R's Dirichlet ghost
+          if (!inside[a][o + 1]) continue;
+          bool okin = true;
+          T w = (T)1;
+          for (int bax = 0; bax < 3; ++bax) {
+            const int oo = bax == a ? o + 1 : 1;
+            okin = okin && inside[bax][oo];
+            w *= bw[bax][oo];
+          }
+          if (!okin || w == (T)0) continue;
+          int yy[3] = {y0[0], y0[1], y0[2]};
+          yy[a] += o;
+          tix[t] = flat(yy, S.ext);
+          const cplx<T> cc = o > 0 ? cf.p[a] : cf.m[a];
+          tcf[t] = mk<T>(w * cc.x, w * cc.y);
+          live |= 1u << t;
+        }
+      }
       for (int k = 0; k < lagd; ++k) {
         if (!want_res && k != lagd - 1) continue;
         const int sl = ring.res_slot[k];
         if (sl < 0) continue;
-        const cplx<T>* u = (const cplx<T>*)ring.p[sl] + lvofs(S, r, (int)gridDim.z);
-        // -(A_R (beta_d u_S))(x)
-        cplx<T> acc = mk<T>(0, 0);
-        {
-          const T w0 = bw[0][1] * bw[1][1] * bw[2][1];
-          if (w0 != (T)0 && inside[0][1] && inside[1][1] && inside[2][1]) {
-            const cplx<T> v = u[flat(y0, S.ext)];
-            cfma(acc, cf.c, mk<T>(w0 * v.x, w0 * v.y));
-          }
+        const cplx<T>* ub = (const cplx<T>*)ring.p[sl];
+#pragma unroll
+        for (int rr = 0; rr < TR_RG; ++rr) {
+          if (rr >= nr) break;
+          const cplx<T>* u = ub + lvofs(S, r0 + rr, nrhs);
+          // -(A_R (beta_d u_S))(x)
+          cplx<T> acc = mk<T>(0, 0);
+#pragma unroll
+          for (int t = 0; t < 7; ++t)
+            if (live & (1u << t)) cfma(acc, tcf[t], u[tix[t]]);
+          if (k == lagd - 1) acc_src[rr] = acc_src[rr] - acc;
+          acc_res[rr] = acc_res[rr] - acc;
         }
-        for (int a = 0; a < dim; ++a) {
-          for (int o = -1; o <= 1; o += 2) {
-            if ((o > 0 && x[a] + 1 >= R.ext[a]) || (o < 0 && x[a] == 0)) continue;   // R's Dirichlet ghost
-            if (!inside[a][o + 1]) continue;
-            bool okin = true;
-            T w = (T)1;
-            for (int bax = 0; bax < 3; ++bax) {
-              const int oo = bax == a ? o + 1 : 1;
-              okin = okin && inside[bax][oo];
-              w *= bw[bax][oo];
-            }
-            if (!okin || w == (T)0) continue;
-            int yy[3] = {y0[0], y0[1], y0[2]};
-            yy[a] += o;
-            const cplx<T> v = u[flat(yy, S.ext)];
-            cfma(acc, o > 0 ? cf.p[a] : cf.m[a], mk<T>(w * v.x, w * v.y));
-          }
-        }
-        if (k == lagd - 1) acc_src = acc_src - acc;
-        acc_res = acc_res - acc;
       }
     }
-    src_next[lvofs(R, r, (int)gridDim.z) + li] = acc_src;
-    if (want_res && (mask & 0x80000000u)) res2 = (double)acc_res.x * acc_res.x + (double)acc_res.y * acc_res.y;
+#pragma unroll
+    for (int rr = 0; rr < TR_RG; ++rr) {
+      if (rr >= nr) break;
+      src_next[lvofs(R, r0 + rr, nrhs) + li] = acc_src[rr];
+      if (want_res && (mask & 0x80000000u))
+        res2[rr] = (double)acc_res[rr].x * acc_res[rr].x + (double)acc_res[rr].y * acc_res[rr].y;
+    }
   }
   if (want_res) {
-    for (int o = 16; o; o >>= 1) res2 += __shfl_xor_sync(0xffffffffu, res2, o);
-    __shared__ double sh[32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = res2;
+    // sums of |res|^2 per block and right-hand side
+#pragma unroll
+    for (int rr = 0; rr < TR_RG; ++rr) {
+      double v = res2[rr];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) sh[rr][threadIdx.x >> 5] = v;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if ((int)threadIdx.x < nr) {
       double t = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-      part[((long long)r * g.nsub + Rid) * gridDim.x + blockIdx.x] = t;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+      part[((long long)(r0 + threadIdx.x) * g.nsub + Rid) * gridDim.x + blockIdx.x] = t;
     }
   }
 }
@@ -199,10 +239,10 @@ static cudaError_t transfer_t(ddm_ctx* c, int s, void* src_next, double* part, i
     int t = s - k;
     rp.res_slot[k] = (k < L && t >= 1) ? (t % L) : -1;
   }
-  dim3 grid((std::max(c->max_scnt, 1) + 127) / 128, c->g.nsub, nrhs);
+  dim3 grid((std::max(c->max_scnt, 1) + 127) / 128, c->g.nsub, (nrhs + TR_RG - 1) / TR_RG);
   if (nblk) *nblk = grid.x;
   ++c->nlaunch;
-  k_transfer<T><<<grid, 128, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res);
+  k_transfer<T><<<grid, 128, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res, nrhs);
   return cudaGetLastError();
 }
 
@@ -229,14 +269,15 @@ __device__ __forceinline__ double cut_hi(const Geom& g, int part, int a, int p) 
   return q < 0 ? 1.0 : (q >= g.ov ? 0.0 : g.beta[q]);
 }
 
+// One thread per global node: its (at most 2 per axis) candidate parts and weights are found
+// once, then applied to every right-hand side, accumulating in the local precision T (the
+// local solutions are only T-accurate; FP64 is what the DDM_FP64 path needs).
 template <typename T>
 __global__ void k_assemble(Geom g, const cplx<T>* U, z64* w, int nrhs) {
-  long long n = g.nglob;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nrhs; i += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(i / n);
-    long long gi = i % n;
+  const long long n = g.nglob;
+  for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < n; gi += (long long)gridDim.x * blockDim.x) {
     int xg[3] = {(int)(gi % g.N[0]), (int)((gi / g.N[0]) % g.N[1]), (int)(gi / ((long long)g.N[0] * g.N[1]))};
-    int cand[3][2], ncand[3], wts_n = 1;
+    int cand[3][2], ncand[3];
     double wt[3][2];
     for (int a = 0; a < 3; ++a) {
       ncand[a] = 0;
@@ -251,22 +292,35 @@ __global__ void k_assemble(Geom g, const cplx<T>* U, z64* w, int nrhs) {
         if (p < g.cuts[a][part] - g.e || p >= g.cuts[a][part + 1] + g.e) bwt = 0.0;
         if (bwt != 0.0 && ncand[a] < 2) { cand[a][ncand[a]] = part; wt[a][ncand[a]] = bwt; ncand[a]++; }
       }
-      wts_n *= ncand[a];
     }
-    z64 acc = mk<double>(0, 0);
-    for (int i0 = 0; i0 < ncand[0]; ++i0)
-      for (int i1 = 0; i1 < ncand[1]; ++i1)
-        for (int i2 = 0; i2 < ncand[2]; ++i2) {
-          int part[3] = {cand[0][i0], cand[1][i1], cand[2][i2]};
-          int sid = (part[2] * g.parts[1] + part[1]) * g.parts[0] + part[0];
-          const SubDesc& s = g.subs[sid];
-          int xl[3] = {xg[0] - s.lo[0], xg[1] - s.lo[1], g.dim == 3 ? xg[2] - s.lo[2] : 0};
-          cplx<T> v = U[lvofs(s, r, nrhs) + flat(xl, s.ext)];
-          double bw = wt[0][i0] * wt[1][i1] * wt[2][i2];
-          acc = acc + bw * mk<double>((double)v.x, (double)v.y);
-        }
-    w[i] = acc;
-    (void)wts_n;
+    // terms t = 4 i0 + 2 i1 + i2 (bit t of `live` when present): element offset of right-hand
+    // side 0, stride between right-hand sides, weight
+    long long tofs[8], tstr[8];
+    T tw[8];
+    unsigned live = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i0 = t >> 2, i1 = (t >> 1) & 1, i2 = t & 1;
+      tofs[t] = 0;
+      tstr[t] = 0;
+      tw[t] = (T)0;
+      if (i0 >= ncand[0] || i1 >= ncand[1] || i2 >= ncand[2]) continue;
+      int part[3] = {cand[0][i0], cand[1][i1], cand[2][i2]};
+      int sid = (part[2] * g.parts[1] + part[1]) * g.parts[0] + part[0];
+      const SubDesc& s = g.subs[sid];
+      int xl[3] = {xg[0] - s.lo[0], xg[1] - s.lo[1], g.dim == 3 ? xg[2] - s.lo[2] : 0};
+      tofs[t] = lvofs(s, 0, nrhs) + flat(xl, s.ext);
+      tstr[t] = (long long)s.ext[0] * s.ext[1] * s.ext[2];
+      tw[t] = (T)(wt[0][i0] * wt[1][i1] * wt[2][i2]);
+      live |= 1u << t;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+      cplx<T> acc = mk<T>(0, 0);
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (live & (1u << t)) acc = acc + tw[t] * U[tofs[t] + r * tstr[t]];
+      w[(long long)r * n + gi] = mk<double>((double)acc.x, (double)acc.y);
+    }
   }
 }
 

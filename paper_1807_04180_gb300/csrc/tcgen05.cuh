@@ -16,6 +16,10 @@ namespace tc {
 
 // bounded waits: tries of mbarrier.try_wait with a suspend-time hint (about 4 s at most)
 constexpr long long TC_WAIT_LIMIT = 1LL << 18;
+// without the hint a try returns after a short system-dependent time; waits on the critical path
+// use it (a thread suspended with a long hint resumes about a microsecond after the phase
+// completes) with a limit on the elapsed time instead of the number of tries
+constexpr unsigned long long TC_SPIN_LIMIT_NS = 2000000000ULL;   // 2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -34,6 +38,34 @@ __device__ __forceinline__ bool bar_try(uint32_t a, uint32_t parity) {
       : "r"(a), "r"(parity), "r"(16384u)
       : "memory");
   return ok != 0;
+}
+__device__ __forceinline__ bool bar_try_nohint(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// as bar_wait_or_abort, spinning without the suspend hint; gives up after TC_SPIN_LIMIT_NS
+__device__ __forceinline__ bool bar_spin_or_abort(uint32_t a, uint32_t parity, volatile int* abort) {
+  if (bar_try_nohint(a, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (bar_try_nohint(a, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (*abort) return false;
+      if (global_ns() - t0 > TC_SPIN_LIMIT_NS) break;
+    }
+  }
+  *abort = 1;
+  return false;
 }
 // waits for the phase of the given parity; false after TC_WAIT_LIMIT tries
 __device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t parity) {

@@ -85,11 +85,10 @@ struct CoefT { cplx<T> c, m[3], p[3]; };
 
 // Each thread takes one strip node of R and TR_RG right-hand sides (blockIdx.z = group): the
 // stencil terms of -A_R (beta_d .) at the node (sender index, coefficient x cut-off) are built
-// once per direction and applied to every right-hand side of the group.
-constexpr int TR_RG = 8;
-
-template <typename T>
-__global__ void __launch_bounds__(128) k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res,
+// once per direction and applied to every right-hand side of the group.  TR_RG = 1 for a single
+// right-hand side (fewer registers, more resident warps), 8 otherwise.
+template <typename T, int TR_RG>
+__global__ void __launch_bounds__(128, TR_RG == 1 ? 6 : 1) k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res,
                                                   int nrhs) {
   const int Rid = blockIdx.y;
   const SubDesc& R = g.subs[Rid];
@@ -239,10 +238,12 @@ static cudaError_t transfer_t(ddm_ctx* c, int s, void* src_next, double* part, i
     int t = s - k;
     rp.res_slot[k] = (k < L && t >= 1) ? (t % L) : -1;
   }
-  dim3 grid((std::max(c->max_scnt, 1) + 127) / 128, c->g.nsub, (nrhs + TR_RG - 1) / TR_RG);
+  const int rg = nrhs == 1 ? 1 : 8;
+  dim3 grid((std::max(c->max_scnt, 1) + 127) / 128, c->g.nsub, (nrhs + rg - 1) / rg);
   if (nblk) *nblk = grid.x;
   ++c->nlaunch;
-  k_transfer<T><<<grid, 128, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res, nrhs);
+  if (rg == 1) k_transfer<T, 1><<<grid, 128, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res, nrhs);
+  else k_transfer<T, 8><<<grid, 128, 0, c->st>>>(c->g, rp, (cplx<T>*)src_next, part, want_res, nrhs);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "ddm_internal.cuh"
 
 namespace ddm {
@@ -202,6 +204,142 @@ __global__ void __launch_bounds__(1024) k_f3_panel(int b, int p0, int w, cplx<T>
   if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
 }
 
+// The same panel elimination spread over a cluster of F3C_N CTAs (planes up to F3C_N x 256 rows
+// wide): CTA q holds rows [q R, (q + 1) R), R = ceil(b / F3C_N), one row per thread in registers.
+// Per pivot: every CTA publishes its best candidate in its shared memory; after a cluster barrier
+// every warp reads the F3C_N candidates through distributed shared memory and picks the pivot row
+// r; the threads holding rows r and c write them into every CTA's shared memory; after a second
+// cluster barrier each thread eliminates column c from its row and forms its candidate for the
+// next pivot.  Every thread of every CTA passes the same barriers (the loop bounds are kernel
+// arguments), so the cluster barriers cannot deadlock.
+constexpr int F3C_N = 8, F3C_T = 256;
+
+template <typename T>
+__global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
+    k_f3_panel_cl(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* err) {
+  namespace cg = cooperative_groups;
+  constexpr int PW = F3Panel<T>::W;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  __shared__ T s_wb[F3C_T / 32];
+  __shared__ int s_wi[F3C_T / 32];
+  __shared__ T s_best;                 // this CTA's candidate, read by every CTA of the cluster
+  __shared__ int s_idx;
+  __shared__ cplx<T> s_row[PW], s_vc[PW];   // pivot row r (raw) and old row c, written by their owners
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int rpc = (b + F3C_N - 1) / F3C_N;
+  const int i = rank * rpc + tid;
+  const bool have = tid < rpc && i < b;
+  cplx<T> R[PW];
+#pragma unroll
+  for (int q = 0; q < PW; ++q) R[q] = (have && q < w) ? W[(long long)i * ldw + p0 + q] : mk<T>(0, 0);
+  if (tid == 0) s_bad = 0;
+  // this CTA's candidate from the per-thread candidates (largest |.|^2, ties to the lowest row)
+  auto cta_candidate = [&](T best, int bi) {
+    for (int o = 16; o; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s_wb[wid] = best; s_wi[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 1; q < F3C_T / 32; ++q)
+        if (s_wb[q] > best || (s_wb[q] == best && s_wi[q] < bi)) { best = s_wb[q]; bi = s_wi[q]; }
+      s_best = best;
+      s_idx = bi;
+    }
+  };
+  {
+    T best = (T)-1;
+    int bi = b;
+    if (have && i >= p0) { best = cabs2(R[0]); bi = i; }
+    cta_candidate(best, bi);
+  }
+  cl.sync();
+#pragma unroll 1
+  for (int qc = 0; qc < w; ++qc) {
+    const int c = p0 + qc;
+    // the cluster's pivot: lane l < F3C_N reads CTA l's candidate
+    T best = (T)-1;
+    int r = b;
+    if (lane < F3C_N) {
+      best = *cl.map_shared_rank(&s_best, (unsigned)lane);
+      r = *cl.map_shared_rank(&s_idx, (unsigned)lane);
+    }
+    for (int o = 16; o; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, r, o);
+      if (ob > best || (ob == best && oi < r)) { best = ob; r = oi; }
+    }
+    const bool ok = best > (T)0 && isfinite(best) && r < b;
+    if (!ok) r = c;
+    // the warps holding rows r and c publish them to every CTA: lane q < PW takes entry q from the
+    // holding lane by shuffle and stores it into each CTA's shared memory
+    auto publish_row = [&](int row, cplx<T>* sbuf) {
+      const int lr = row - rank * rpc;
+      if (lr < 0 || lr >= rpc || wid != (lr >> 5)) return;   // warp-uniform
+      const int src = lr & 31;
+      cplx<T> mine = mk<T>(0, 0);
+#pragma unroll
+      for (int q = 0; q < PW; ++q) {
+        const T x = __shfl_sync(0xffffffffu, R[q].x, src);
+        const T y = __shfl_sync(0xffffffffu, R[q].y, src);
+        if (lane == q) mine = mk<T>(x, y);
+      }
+      if (lane < PW)
+        for (int d = 0; d < F3C_N; ++d) cl.map_shared_rank(sbuf, (unsigned)d)[lane] = mine;
+    };
+    publish_row(r, s_row);
+    publish_row(c, s_vc);
+    if (rank == 0 && tid == 0) {
+      perm[c] = r;
+      if (!ok) s_bad = 1;
+    }
+    cl.sync();
+    const cplx<T> inv = ok ? cinv(s_row[qc]) : mk<T>(0, 0);
+    // interchange and elimination of column qc on this thread's row; candidate of the next pivot
+    T nb = (T)-1;
+    int ni = b;
+    if (have) {
+      if (i == c) {
+#pragma unroll
+        for (int q = 0; q < PW; ++q) R[q] = q == qc ? inv : s_row[q] * inv;
+      } else {
+        if (i == r) {
+#pragma unroll
+          for (int q = 0; q < PW; ++q) R[q] = s_vc[q];   // row r takes old row c
+        }
+        cplx<T> fi = mk<T>(0, 0);
+#pragma unroll
+        for (int q = 0; q < PW; ++q)
+          if (q == qc) fi = -R[q];
+        const cplx<T> fiv = fi * inv;
+#pragma unroll
+        for (int q = 0; q < PW; ++q) {
+          if (q == qc) R[q] = fiv;
+          else cfma(R[q], fiv, s_row[q]);    // fi rs[q] = (fi inv) s_row[q]
+        }
+        if (i > c && qc + 1 < w) {
+          cplx<T> nx = mk<T>(0, 0);
+#pragma unroll
+          for (int q = 0; q < PW; ++q)
+            if (q == qc + 1) nx = R[q];
+          nb = cabs2(nx);
+          ni = i;
+        }
+      }
+    }
+    cta_candidate(nb, ni);
+    cl.sync();
+  }
+#pragma unroll
+  for (int q = 0; q < PW; ++q)
+    if (have && q < w) W[(long long)i * ldw + p0 + q] = R[q];
+  if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
+}
+
 // thread per column j outside the panel: the panel's interchanges in order, then the old pivot
 // rows into Tp (w x ldw) and zero in W
 template <typename T>
@@ -320,7 +458,8 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
         for (int p0 = 0; p0 < b; p0 += PW) {
           const int w = std::min(PW, b - p0);
           c->nlaunch += 3;
-          k_f3_panel<T><<<1, 1024, psm, c->st>>>(b, p0, w, W, ldw, perm, c->d_err);
+          if (b <= F3C_N * F3C_T) k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p0, w, W, ldw, perm, c->d_err);
+          else k_f3_panel<T><<<1, 1024, psm, c->st>>>(b, p0, w, W, ldw, perm, c->d_err);
           k_f3_swap<T><<<(b + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, perm, Tp);
           k_f3_rankw<T><<<gr, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp);
         }

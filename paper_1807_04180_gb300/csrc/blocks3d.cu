@@ -216,7 +216,7 @@ constexpr int F3C_N = 8, F3C_T = 256;
 
 template <typename T>
 __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
-    k_f3_panel_cl(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* err) {
+    k_f3_panel_cl(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* swl, int* err) {
   namespace cg = cooperative_groups;
   constexpr int PW = F3Panel<T>::W;
   cg::cluster_group cl = cg::this_cluster();
@@ -226,7 +226,7 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
   __shared__ T s_best;                 // this CTA's candidate, read by every CTA of the cluster
   __shared__ int s_idx;
   __shared__ cplx<T> s_row[PW], s_vc[PW];   // pivot row r (raw) and old row c, written by their owners
-  __shared__ int s_bad;
+  __shared__ int s_bad, s_perm[PW];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int rpc = (b + F3C_N - 1) / F3C_N;
   const int i = rank * rpc + tid;
@@ -295,6 +295,7 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
     publish_row(c, s_vc);
     if (rank == 0 && tid == 0) {
       perm[c] = r;
+      s_perm[qc] = r;
       if (!ok) s_bad = 1;
     }
     cl.sync();
@@ -338,6 +339,65 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
   for (int q = 0; q < PW; ++q)
     if (have && q < w) W[(long long)i * ldw + p0 + q] = R[q];
   if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
+  if (rank == 0 && wid == 0) {
+    // compose the panel's interchanges into (destination, source) rows for k_f3_gather: lane t
+    // holds one touched row (the panel's rows first) and the row its content comes from
+    int row_l = lane < w ? p0 + lane : -1, src_l = row_l, n = w;
+    for (int qc = 0; qc < w; ++qc) {
+      const int pr = s_perm[qc];
+      const unsigned m = __ballot_sync(0xffffffffu, row_l == pr);
+      int bb;
+      if (m) {
+        bb = __ffs(m) - 1;
+      } else {
+        bb = n;
+        if (lane == n) { row_l = pr; src_l = pr; }
+        ++n;
+      }
+      const int sa = __shfl_sync(0xffffffffu, src_l, qc), sb = __shfl_sync(0xffffffffu, src_l, bb);
+      if (lane == qc) src_l = sb;
+      if (lane == bb) src_l = sa;
+    }
+    const bool emit = lane < n && (lane < w || src_l != row_l);
+    const unsigned em = __ballot_sync(0xffffffffu, emit);
+    const int pos = __popc(em & ((1u << lane) - 1u));
+    if (emit) { swl[1 + 2 * pos] = row_l; swl[2 + 2 * pos] = src_l; }
+    if (lane == 0) swl[0] = __popc(em);
+  }
+}
+
+// thread per column j outside the panel, driven by the list of k_f3_panel_cl: every moved row's
+// source is loaded first, then the old pivot rows go to Tp (w x ldw) and are zeroed in W and the
+// other moved rows are written in place
+template <typename T>
+__global__ void k_f3_gather(int b, int p0, int w, cplx<T>* W, int ldw, const int* swl, cplx<T>* Tp) {
+  constexpr int PW = F3Panel<T>::W;
+  __shared__ int s_dst[2 * PW], s_src[2 * PW], s_n;
+  if (threadIdx.x == 0) s_n = swl[0];
+  if (threadIdx.x < 2 * PW) {
+    s_dst[threadIdx.x] = swl[1 + 2 * threadIdx.x];
+    s_src[threadIdx.x] = swl[2 + 2 * threadIdx.x];
+  }
+  __syncthreads();
+  const int n = s_n;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b; j += gridDim.x * blockDim.x) {
+    if (j >= p0 && j < p0 + w) continue;
+    cplx<T> v[2 * PW];
+#pragma unroll
+    for (int t = 0; t < 2 * PW; ++t)
+      if (t < n) v[t] = W[(long long)s_src[t] * ldw + j];
+#pragma unroll
+    for (int t = 0; t < 2 * PW; ++t) {
+      if (t >= n) break;
+      const int d = s_dst[t];
+      if (d >= p0 && d < p0 + w) {
+        Tp[(long long)(d - p0) * ldw + j] = v[t];
+        W[(long long)d * ldw + j] = mk<T>(0, 0);
+      } else {
+        W[(long long)d * ldw + j] = v[t];
+      }
+    }
+  }
 }
 
 // thread per column j outside the panel: the panel's interchanges in order, then the old pivot
@@ -442,6 +502,8 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   if ((e = cudaMalloc((void**)&st, sizeof(F3State))) != cudaSuccess) return e;
   constexpr int PW = F3Panel<T>::W;
   cplx<T>* Tp = nullptr;
+  int* swl = nullptr;
+  if ((e = cudaMalloc((void**)&swl, sizeof(int) * (4 * PW + 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc((void**)&Tp, sizeof(cplx<T>) * (size_t)PW * ldw)) != cudaSuccess) return e;
   const size_t psm = f3_panel_smem(bmax, (int)sizeof(cplx<T>));
   const bool blocked = psm <= 220 * 1024;
@@ -458,9 +520,13 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
         for (int p0 = 0; p0 < b; p0 += PW) {
           const int w = std::min(PW, b - p0);
           c->nlaunch += 3;
-          if (b <= F3C_N * F3C_T) k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p0, w, W, ldw, perm, c->d_err);
-          else k_f3_panel<T><<<1, 1024, psm, c->st>>>(b, p0, w, W, ldw, perm, c->d_err);
-          k_f3_swap<T><<<(b + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, perm, Tp);
+          if (b <= F3C_N * F3C_T) {
+            k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p0, w, W, ldw, perm, swl, c->d_err);
+            k_f3_gather<T><<<(b + 127) / 128, 128, 0, c->st>>>(b, p0, w, W, ldw, swl, Tp);
+          } else {
+            k_f3_panel<T><<<1, 1024, psm, c->st>>>(b, p0, w, W, ldw, perm, c->d_err);
+            k_f3_swap<T><<<(b + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, perm, Tp);
+          }
           k_f3_rankw<T><<<gr, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp);
         }
       } else {
@@ -479,7 +545,7 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
     }
   }
   cudaStreamSynchronize(c->st);
-  cudaFree(W); cudaFree(colp); cudaFree(perm); cudaFree(cm); cudaFree(st); cudaFree(Tp);
+  cudaFree(W); cudaFree(colp); cudaFree(perm); cudaFree(cm); cudaFree(st); cudaFree(Tp); cudaFree(swl);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

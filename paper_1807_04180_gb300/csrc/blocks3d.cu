@@ -206,12 +206,13 @@ __global__ void __launch_bounds__(1024) k_f3_panel(int b, int p0, int w, cplx<T>
 
 // The same panel elimination spread over a cluster of F3C_N CTAs (planes up to F3C_N x 256 rows
 // wide): CTA q holds rows [q R, (q + 1) R), R = ceil(b / F3C_N), one row per thread in registers.
-// Per pivot: every CTA publishes its best candidate in its shared memory; after a cluster barrier
-// every warp reads the F3C_N candidates through distributed shared memory and picks the pivot row
-// r; the threads holding rows r and c write them into every CTA's shared memory; after a second
-// cluster barrier each thread eliminates column c from its row and forms its candidate for the
-// next pivot.  Every thread of every CTA passes the same barriers (the loop bounds are kernel
-// arguments), so the cluster barriers cannot deadlock.
+// One cluster barrier per pivot: after eliminating pivot c, every CTA writes its best candidate
+// for pivot c + 1 (value, row index and the row's panel values) into its slot of every CTA's
+// shared memory, and the holder of row c + 1 writes that row too; after the barrier each CTA
+// picks the pivot among the F3C_N slots and has the pivot row and the old row c + 1 locally.  The
+// slots alternate between two buffers by pivot parity, so a slot is rewritten only after every
+// CTA has passed the barrier that follows its last read.  Every thread of every CTA passes the
+// same barriers (the loop bounds are kernel arguments), so the cluster barriers cannot deadlock.
 constexpr int F3C_N = 8, F3C_T = 256;
 
 template <typename T>
@@ -223,9 +224,13 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
   const int rank = (int)cl.block_rank();
   __shared__ T s_wb[F3C_T / 32];
   __shared__ int s_wi[F3C_T / 32];
-  __shared__ T s_best;                 // this CTA's candidate, read by every CTA of the cluster
+  __shared__ T s_best;
   __shared__ int s_idx;
-  __shared__ cplx<T> s_row[PW], s_vc[PW];   // pivot row r (raw) and old row c, written by their owners
+  // slots written by the cluster's CTAs: candidate value, row and panel values per CTA; row c
+  __shared__ T s_cv[2][F3C_N];
+  __shared__ int s_ci[2][F3C_N];
+  __shared__ cplx<T> s_crow[2][F3C_N][PW];
+  __shared__ cplx<T> s_rowc[2][PW];
   __shared__ int s_bad, s_perm[PW];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int rpc = (b + F3C_N - 1) / F3C_N;
@@ -235,8 +240,24 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
 #pragma unroll
   for (int q = 0; q < PW; ++q) R[q] = (have && q < w) ? W[(long long)i * ldw + p0 + q] : mk<T>(0, 0);
   if (tid == 0) s_bad = 0;
-  // this CTA's candidate from the per-thread candidates (largest |.|^2, ties to the lowest row)
-  auto cta_candidate = [&](T best, int bi) {
+  // the warp holding local row lr sends that row's panel values to dst(d) in every CTA d
+  auto send_row = [&](int row, auto dst) {
+    const int lr = row - rank * rpc;
+    if (row < 0 || row >= b || lr < 0 || lr >= rpc || wid != (lr >> 5)) return;   // warp-uniform
+    const int src = lr & 31;
+    cplx<T> mine = mk<T>(0, 0);
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+      const T x = __shfl_sync(0xffffffffu, R[q].x, src);
+      const T y = __shfl_sync(0xffffffffu, R[q].y, src);
+      if (lane == q) mine = mk<T>(x, y);
+    }
+    if (lane < PW)
+      for (int d = 0; d < F3C_N; ++d) dst((unsigned)d)[lane] = mine;
+  };
+  // this CTA's best candidate (largest |.|^2, ties to the lowest row) into slot buf of every CTA,
+  // with its row; and row c into every CTA's s_rowc[buf]
+  auto publish = [&](T best, int bi, int buf, int c) {
     for (int o = 16; o; o >>= 1) {
       const T ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -250,67 +271,56 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
       s_best = best;
       s_idx = bi;
     }
+    __syncthreads();
+    const int cb = s_idx;
+    if (tid < F3C_N) {
+      *cl.map_shared_rank(&s_cv[buf][rank], (unsigned)tid) = s_best;
+      *cl.map_shared_rank(&s_ci[buf][rank], (unsigned)tid) = cb;
+    }
+    send_row(cb, [&](unsigned d) { return cl.map_shared_rank(&s_crow[buf][rank][0], d); });
+    send_row(c, [&](unsigned d) { return cl.map_shared_rank(&s_rowc[buf][0], d); });
   };
   {
     T best = (T)-1;
     int bi = b;
     if (have && i >= p0) { best = cabs2(R[0]); bi = i; }
-    cta_candidate(best, bi);
+    publish(best, bi, 0, p0);
   }
   cl.sync();
 #pragma unroll 1
   for (int qc = 0; qc < w; ++qc) {
-    const int c = p0 + qc;
-    // the cluster's pivot: lane l < F3C_N reads CTA l's candidate
-    T best = (T)-1;
-    int r = b;
-    if (lane < F3C_N) {
-      best = *cl.map_shared_rank(&s_best, (unsigned)lane);
-      r = *cl.map_shared_rank(&s_idx, (unsigned)lane);
-    }
+    const int c = p0 + qc, buf = qc & 1;
+    // the cluster's pivot from the slots (every warp alike): lane l < F3C_N reads CTA l's slot
+    T best = lane < F3C_N ? s_cv[buf][lane] : (T)-1;
+    int r = lane < F3C_N ? s_ci[buf][lane] : b;
+    int k = lane < F3C_N ? lane : F3C_N;
     for (int o = 16; o; o >>= 1) {
       const T ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, r, o);
-      if (ob > best || (ob == best && oi < r)) { best = ob; r = oi; }
+      const int ok2 = __shfl_xor_sync(0xffffffffu, k, o);
+      if (ob > best || (ob == best && oi < r)) { best = ob; r = oi; k = ok2; }
     }
-    const bool ok = best > (T)0 && isfinite(best) && r < b;
-    if (!ok) r = c;
-    // the warps holding rows r and c publish them to every CTA: lane q < PW takes entry q from the
-    // holding lane by shuffle and stores it into each CTA's shared memory
-    auto publish_row = [&](int row, cplx<T>* sbuf) {
-      const int lr = row - rank * rpc;
-      if (lr < 0 || lr >= rpc || wid != (lr >> 5)) return;   // warp-uniform
-      const int src = lr & 31;
-      cplx<T> mine = mk<T>(0, 0);
-#pragma unroll
-      for (int q = 0; q < PW; ++q) {
-        const T x = __shfl_sync(0xffffffffu, R[q].x, src);
-        const T y = __shfl_sync(0xffffffffu, R[q].y, src);
-        if (lane == q) mine = mk<T>(x, y);
-      }
-      if (lane < PW)
-        for (int d = 0; d < F3C_N; ++d) cl.map_shared_rank(sbuf, (unsigned)d)[lane] = mine;
-    };
-    publish_row(r, s_row);
-    publish_row(c, s_vc);
+    const bool ok = best > (T)0 && isfinite(best) && r < b && k < F3C_N;
+    if (!ok) { r = c; k = 0; }
+    const cplx<T>* prow = s_crow[buf][k];      // old row r
+    const cplx<T>* vc = s_rowc[buf];           // old row c
     if (rank == 0 && tid == 0) {
       perm[c] = r;
       s_perm[qc] = r;
       if (!ok) s_bad = 1;
     }
-    cl.sync();
-    const cplx<T> inv = ok ? cinv(s_row[qc]) : mk<T>(0, 0);
+    const cplx<T> inv = ok ? cinv(prow[qc]) : mk<T>(0, 0);
     // interchange and elimination of column qc on this thread's row; candidate of the next pivot
     T nb = (T)-1;
     int ni = b;
     if (have) {
       if (i == c) {
 #pragma unroll
-        for (int q = 0; q < PW; ++q) R[q] = q == qc ? inv : s_row[q] * inv;
+        for (int q = 0; q < PW; ++q) R[q] = q == qc ? inv : prow[q] * inv;
       } else {
         if (i == r) {
 #pragma unroll
-          for (int q = 0; q < PW; ++q) R[q] = s_vc[q];   // row r takes old row c
+          for (int q = 0; q < PW; ++q) R[q] = vc[q];   // row r takes old row c
         }
         cplx<T> fi = mk<T>(0, 0);
 #pragma unroll
@@ -320,7 +330,7 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
 #pragma unroll
         for (int q = 0; q < PW; ++q) {
           if (q == qc) R[q] = fiv;
-          else cfma(R[q], fiv, s_row[q]);    // fi rs[q] = (fi inv) s_row[q]
+          else cfma(R[q], fiv, prow[q]);    // fi rs[q] = (fi inv) prow[q]
         }
         if (i > c && qc + 1 < w) {
           cplx<T> nx = mk<T>(0, 0);
@@ -332,8 +342,10 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
         }
       }
     }
-    cta_candidate(nb, ni);
-    cl.sync();
+    if (qc + 1 < w) {
+      publish(nb, ni, buf ^ 1, c + 1);
+      cl.sync();
+    }
   }
 #pragma unroll
   for (int q = 0; q < PW; ++q)

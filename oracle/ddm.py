@@ -9,7 +9,7 @@ array index p + e of the global extended grid.  A subdomain R has index tuple
 the extended node range [lo_a - e, hi_a + e), i.e. the global array window
 [lo_a, hi_a + 2e).
 
-Readings of the paper taken here (each is also listed in the design doc):
+Readings of the paper taken here (where it is silent, ambiguous or garbled):
   * cut-offs: beta_0(t) = 1 - (10 t^3 - 15 t^4 + 6 t^5) on [0, 1], clamped
     (C^2, monotone, 1 for t <= 0, 0 for t >= 1, as Section 2.2 requires); a
     node q = 0, 1, .. nodes beyond a face (q = 0: first node outside) gets

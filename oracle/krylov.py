@@ -4,7 +4,7 @@ Test infrastructure: see the package docstring.
 
 Section 4.2.2 uses Algorithm 3.1 as a preconditioner of flexible GMRES with K
 DDM steps per application and reports the GMRES iteration count.  The paper
-gives no further detail; the readings used here (also in the design doc):
+gives no further detail; the readings used here:
 x_0 = 0, restart length m, classical Gram-Schmidt applied twice (CGS2) for the
 Arnoldi step, Givens rotations for the least-squares problem, and the stop
 test |g_{j+1}| / ||b|| <= tol on the least-squares residual estimate.

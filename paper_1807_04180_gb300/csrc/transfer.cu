@@ -86,9 +86,11 @@ struct CoefT { cplx<T> c, m[3], p[3]; };
 // Each thread takes one strip node of R and TR_RG right-hand sides (blockIdx.z = group): the
 // stencil terms of -A_R (beta_d .) at the node (sender index, coefficient x cut-off) are built
 // once per direction and applied to every right-hand side of the group.  TR_RG = 1 for a single
-// right-hand side (fewer registers, more resident warps), 8 otherwise.
+// right-hand side (fewer registers, more resident warps), 8 otherwise.  The kernel is bound by the
+// latency of its gathered loads, so the register caps favour resident warps over a small spill
+// (2048^2, 64 right-hand sides: 2.09 ms per transfer at 96 registers against 2.60 ms at 141).
 template <typename T, int TR_RG>
-__global__ void __launch_bounds__(128, TR_RG == 1 ? 6 : 1) k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res,
+__global__ void __launch_bounds__(128, TR_RG == 1 ? 6 : 5) k_transfer(Geom g, RingPtrs ring, cplx<T>* src_next, double* part, int want_res,
                                                   int nrhs) {
   const int Rid = blockIdx.y;
   const SubDesc& R = g.subs[Rid];

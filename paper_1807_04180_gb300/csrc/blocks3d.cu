@@ -115,94 +115,17 @@ __global__ void k_f3_update(int b, int p, cplx<T>* W, int ldw, const cplx<T>* co
 
 // Blocked Gauss-Jordan on W (the same block step as the 2D factor, for 3D's wide plane blocks).
 // For a panel P = [p0, p0 + w):
-//  1. k_f3_panel: one CTA holds the panel's columns (all b rows) in shared memory and runs the
-//     unblocked elimination on them (pivot search over rows >= c, interchange, scaling,
+//  1. k_f3_panel_cl: a cluster of CTAs holds the panel's columns (all b rows) in registers and
+//     runs the unblocked elimination on them (pivot search over rows >= c, interchange, scaling,
 //     elimination of column c from every other row); the panel then holds the new column block
-//     of the inverse;
-//  2. k_f3_swap: the panel's interchanges on the other columns, in order; the old pivot rows are
-//     saved in Tp (w x b) and zeroed in W;
+//     of the inverse, and the panel's interchanges are composed into a list of moved rows;
+//  2. k_f3_gather: the interchanges on the other columns; the old pivot rows are saved in Tp
+//     (w x b) and zeroed in W;
 //  3. k_f3_rankw: every other column takes the w elimination steps at once,
 //     W[i][j] += sum_q W[i][p0 + q] Tp[q][j]  (for the pivot rows this is their new value).
 // Three launches per panel instead of two per pivot.
 template <typename T> struct F3Panel { static constexpr int W = 16; };
 template <> struct F3Panel<double> { static constexpr int W = 8; };
-
-size_t f3_panel_smem(int b, int elem) { return (size_t)b * ((elem == 8 ? 16 : 8) + 1) * elem; }
-
-template <typename T>
-__global__ void __launch_bounds__(1024) k_f3_panel(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* err) {
-  constexpr int PW = F3Panel<T>::W, LD = PW + 1;   // padded rows: one thread per row is conflict-free
-  extern __shared__ unsigned char f3sm[];
-  cplx<T>* P = reinterpret_cast<cplx<T>*>(f3sm);   // P[i LD + q] = W[i][p0 + q]
-  __shared__ T sbest[32];
-  __shared__ int sidx[32];
-  __shared__ int s_r, s_bad;
-  __shared__ cplx<T> s_rs[PW], s_inv;
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  for (int idx = tid; idx < b * PW; idx += nth) {
-    const int i = idx / PW, q = idx - i * PW;
-    P[i * LD + q] = q < w ? W[(long long)i * ldw + p0 + q] : mk<T>(0, 0);
-  }
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-  for (int qc = 0; qc < w; ++qc) {
-    const int c = p0 + qc;
-    // pivot: largest |P[i][qc]| over rows i >= c (ties to the lowest row)
-    T best = (T)-1;
-    int bi = c;
-    for (int i = c + tid; i < b; i += nth) {
-      const T a = cabs2(P[i * LD + qc]);
-      if (a > best) { best = a; bi = i; }
-    }
-    for (int o = 16; o; o >>= 1) {
-      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (lane == 0) { sbest[wid] = best; sidx[wid] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      for (int q = 1; q < (nth >> 5); ++q)
-        if (sbest[q] > best || (sbest[q] == best && sidx[q] < bi)) { best = sbest[q]; bi = sidx[q]; }
-      s_r = bi;
-      perm[c] = bi;
-      if (!(best > (T)0) || !isfinite(best)) { s_bad = 1; s_inv = mk<T>(0, 0); }
-      else s_inv = cinv(P[bi * LD + qc]);
-    }
-    __syncthreads();
-    const int r = s_r;
-    // interchange rows c and r; the pivot row (old row r) scaled becomes row c
-    if (tid < PW) {
-      const cplx<T> inv = s_inv;
-      const cplx<T> vc = P[c * LD + tid], vr = P[r * LD + tid];
-      const cplx<T> rs = tid == qc ? inv : vr * inv;
-      s_rs[tid] = rs;
-      if (r != c) P[r * LD + tid] = vc;
-      P[c * LD + tid] = rs;
-    }
-    __syncthreads();
-    // eliminate column qc from every other row
-    {
-      const cplx<T> inv = s_inv;
-      for (int i = tid; i < b; i += nth) {
-        if (i == c) continue;
-        const cplx<T> fi = -P[i * LD + qc];
-#pragma unroll
-        for (int q = 0; q < PW; ++q) {
-          if (q >= w) break;
-          if (q == qc) P[i * LD + q] = fi * inv;
-          else cfma(P[i * LD + q], fi, s_rs[q]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < b * PW; idx += nth) {
-    const int i = idx / PW, q = idx - i * PW;
-    if (q < w) W[(long long)i * ldw + p0 + q] = P[i * LD + q];
-  }
-  if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
-}
 
 // The same panel elimination spread over a cluster of F3C_N CTAs (planes up to F3C_N x 256 rows
 // wide): CTA q holds rows [q R, (q + 1) R), R = ceil(b / F3C_N), one row per thread in registers.
@@ -412,27 +335,6 @@ __global__ void k_f3_gather(int b, int p0, int w, cplx<T>* W, int ldw, const int
   }
 }
 
-// thread per column j outside the panel: the panel's interchanges in order, then the old pivot
-// rows into Tp (w x ldw) and zero in W
-template <typename T>
-__global__ void k_f3_swap(int b, int p0, int w, cplx<T>* W, int ldw, const int* perm, cplx<T>* Tp) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b; j += gridDim.x * blockDim.x) {
-    if (j >= p0 && j < p0 + w) continue;
-    for (int c = p0; c < p0 + w; ++c) {
-      const int r = perm[c];
-      if (r != c) {
-        const cplx<T> t0 = W[(long long)c * ldw + j];
-        W[(long long)c * ldw + j] = W[(long long)r * ldw + j];
-        W[(long long)r * ldw + j] = t0;
-      }
-    }
-    for (int q = 0; q < w; ++q) {
-      Tp[(long long)q * ldw + j] = W[(long long)(p0 + q) * ldw + j];
-      W[(long long)(p0 + q) * ldw + j] = mk<T>(0, 0);
-    }
-  }
-}
-
 // W[i][j] += sum_q W[i][p0 + q] Tp[q][j] for the columns j outside the panel: 64 x 64 tiles,
 // 256 threads, 4 x 4 outputs each (rows ty + 16 a, columns tx + 16 c)
 template <typename T>
@@ -517,9 +419,9 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   int* swl = nullptr;
   if ((e = cudaMalloc((void**)&swl, sizeof(int) * (4 * PW + 1))) != cudaSuccess) return e;
   if ((e = cudaMalloc((void**)&Tp, sizeof(cplx<T>) * (size_t)PW * ldw)) != cudaSuccess) return e;
-  const size_t psm = f3_panel_smem(bmax, (int)sizeof(cplx<T>));
-  const bool blocked = psm <= 220 * 1024;
-  if (blocked && (e = allow_dynamic_smem((const void*)k_f3_panel<T>, psm)) != cudaSuccess) return e;
+  // blocked when every plane block fits the cluster panel (b <= 2048); wider planes one pivot at
+  // a time
+  const bool blocked = bmax <= F3C_N * F3C_T;
   cplx<T>* G = (cplx<T>*)c->d_G;
   for (size_t f = 0; f < reps.size(); ++f) {
     const int b = c->fac_b[f], m = c->fac_m[f], ldb = c->fac_ldb[f];
@@ -532,17 +434,12 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
         for (int p0 = 0; p0 < b; p0 += PW) {
           const int w = std::min(PW, b - p0);
           c->nlaunch += 3;
-          if (b <= F3C_N * F3C_T) {
-            k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p0, w, W, ldw, perm, swl, c->d_err);
-            k_f3_gather<T><<<(b + 127) / 128, 128, 0, c->st>>>(b, p0, w, W, ldw, swl, Tp);
-          } else {
-            k_f3_panel<T><<<1, 1024, psm, c->st>>>(b, p0, w, W, ldw, perm, c->d_err);
-            k_f3_swap<T><<<(b + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, perm, Tp);
-          }
+          k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p0, w, W, ldw, perm, swl, c->d_err);
+          k_f3_gather<T><<<(b + 127) / 128, 128, 0, c->st>>>(b, p0, w, W, ldw, swl, Tp);
           k_f3_rankw<T><<<gr, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp);
         }
       } else {
-        // planes too wide for a shared-memory panel: one pivot at a time
+        // planes too wide for the cluster panel: one pivot at a time
         for (int p = 0; p < b; ++p) {
           c->nlaunch += 2;
           k_f3_pivot<T><<<1, 1024, 0, c->st>>>(b, p, W, ldw, colp, perm, st, c->d_err);

@@ -89,19 +89,13 @@ __global__ void __launch_bounds__(FAC_THREADS, sizeof(T) == 4 ? 2 : 1) k_factor2
     // every other column j takes the same w elimination steps at once:
     //   rows i outside P:  M[i][j] += sum_q M[i][p0+q] T[q][j]
     //   rows of P:         M[p0+q'][j] = sum_q M[p0+q'][p0+q] T[q][j]
-    // (the block Gauss-Jordan step; three barriers per panel instead of three per pivot)
-    for (int p0 = 0; p0 < b; p0 += FAC_W) {
-      const int w = min(FAC_W, b - p0);
-      if (warp == 0) {
-        // the panel in registers: R[t][q] = M[lane + 32 t][p0 + q]
-        cplx<T> R[4][FAC_W];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-          for (int q = 0; q < FAC_W; ++q) {
-            const int i = lane + 32 * t;
-            R[t][q] = (i < b && q < w) ? M[i * ldm + p0 + q] : mk<T>(0, 0);
-          }
+    // (the block Gauss-Jordan step)
+    // Look-ahead: after panel p's interchanges, warp 0 applies panel p's step to the next panel's
+    // columns in its registers and eliminates that panel, while the other warps apply panel p's
+    // step to the remaining columns (two barriers per panel; the elimination of a panel by one
+    // warp runs beside the update instead of before it).
+    cplx<T> R[4][FAC_W];    // warp 0's panel: R[t][q] = M[lane + 32 t][p0 + q]
+    auto eliminate = [&](const int p0, const int w) {
 #pragma unroll
         for (int qc = 0; qc < FAC_W; ++qc) {
           if (qc >= w) break;
@@ -179,8 +173,22 @@ __global__ void __launch_bounds__(FAC_THREADS, sizeof(T) == 4 ? 2 : 1) k_factor2
             const int i = lane + 32 * t;
             if (i < b && q < w) M[i * ldm + p0 + q] = R[t][q];
           }
-      }
-      __syncthreads();
+    };
+    if (warp == 0) {
+      const int w = min(FAC_W, b);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int q = 0; q < FAC_W; ++q) {
+          const int i = lane + 32 * t;
+          R[t][q] = (i < b && q < w) ? M[i * ldm + q] : mk<T>(0, 0);
+        }
+      eliminate(0, w);
+    }
+    __syncthreads();
+    for (int p0 = 0; p0 < b; p0 += FAC_W) {
+      const int w = min(FAC_W, b - p0);
+      const int p1 = p0 + w, w1 = min(FAC_W, b - p1);   // the next panel (none when w1 <= 0)
       // the panel's interchanges on the other columns, in order, and the old pivot rows
       for (int j = tid; j < b; j += nth) {
         if (j >= p0 && j < p0 + w) continue;
@@ -195,22 +203,50 @@ __global__ void __launch_bounds__(FAC_THREADS, sizeof(T) == 4 ? 2 : 1) k_factor2
         for (int q = 0; q < w; ++q) Tp[q * ldm + j] = M[(p0 + q) * ldm + j];
       }
       __syncthreads();
-      // rank-w update of the other columns: warp per row set, lanes over columns (the pivot
-      // rows' old values read from Tp, conflict-free along the lanes)
-      for (int i = warp; i < b; i += nwarp) {
-        const bool prow = i >= p0 && i < p0 + w;
-        cplx<T> mi[FAC_W];
+      if (w1 > 0 && warp == 0) {
+        // the next panel's columns take this panel's step (same arithmetic and order as below)
 #pragma unroll
-        for (int q = 0; q < FAC_W; ++q) mi[q] = q < w ? M[i * ldm + p0 + q] : mk<T>(0, 0);
+        for (int t = 0; t < 4; ++t) {
+          const int i = lane + 32 * t;
+          const bool prow = i >= p0 && i < p0 + w;
+          cplx<T> mi[FAC_W];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int j = lane + 32 * jj;
-          if (jj < njj && j < b && (j < p0 || j >= p0 + w)) {
-            cplx<T> acc = prow ? mk<T>(0, 0) : M[i * ldm + j];
+          for (int q = 0; q < FAC_W; ++q) mi[q] = (i < b && q < w) ? M[i * ldm + p0 + q] : mk<T>(0, 0);
 #pragma unroll
-            for (int q = 0; q < FAC_W; ++q)
-              if (q < w) cfma(acc, mi[q], Tp[q * ldm + j]);
-            M[i * ldm + j] = acc;
+          for (int q1 = 0; q1 < FAC_W; ++q1) {
+            cplx<T> acc = mk<T>(0, 0);
+            if (i < b && q1 < w1) {
+              const int j = p1 + q1;
+              acc = prow ? mk<T>(0, 0) : M[i * ldm + j];
+#pragma unroll
+              for (int q = 0; q < FAC_W; ++q)
+                if (q < w) cfma(acc, mi[q], Tp[q * ldm + j]);
+            }
+            R[t][q1] = acc;
+          }
+        }
+        eliminate(p1, w1);
+      } else {
+        // rank-w update of the other columns: warp per row set, lanes over columns (the pivot
+        // rows' old values read from Tp, conflict-free along the lanes); the next panel's
+        // columns are warp 0's
+        const int busy = w1 > 0 ? 1 : 0;
+        const int lo = w1 > 0 ? p1 : b, hi = w1 > 0 ? p1 + w1 : b;
+        for (int i = warp - busy; i < b; i += nwarp - busy) {
+          const bool prow = i >= p0 && i < p0 + w;
+          cplx<T> mi[FAC_W];
+#pragma unroll
+          for (int q = 0; q < FAC_W; ++q) mi[q] = q < w ? M[i * ldm + p0 + q] : mk<T>(0, 0);
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = lane + 32 * jj;
+            if (jj < njj && j < b && (j < p0 || j >= p0 + w) && (j < lo || j >= hi)) {
+              cplx<T> acc = prow ? mk<T>(0, 0) : M[i * ldm + j];
+#pragma unroll
+              for (int q = 0; q < FAC_W; ++q)
+                if (q < w) cfma(acc, mi[q], Tp[q * ldm + j]);
+              M[i * ldm + j] = acc;
+            }
           }
         }
       }

@@ -6,8 +6,10 @@
 // U_k = diag(c_zp) between planes.  As in 2D the factor keeps G_k = D_k^{-1},
 // D_k = T_k - L_k G_{k-1} U_{k-1}, column-major with leading dimension ldb; here a block
 // (1444 x 1444 for 38^3 subdomains) lives in global memory (it stays in L2) and is inverted by
-// Gauss-Jordan with partial pivoting, one interchange kernel and one rank-1 update kernel per
-// pivot.  The solve applies the blocks to every right-hand side that shares the factor at once
+// blocked Gauss-Jordan with partial pivoting: 16-column panels eliminated by a thread-block
+// cluster, the panel's interchanges, and a tiled rank-16 update of the other columns (one pivot
+// at a time, an interchange and a rank-1 update kernel per pivot, for planes wider than the
+// cluster panel covers).  The solve applies the blocks to every right-hand side that shares the factor at once
 // (a GEMM per plane, right-hand sides as columns) with the Schur coupling fused into the
 // operand load and the t / x / U updates fused into the epilogue.
 #include <algorithm>

@@ -407,20 +407,34 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   int bmax = 0;
   for (size_t f = 0; f < reps.size(); ++f) bmax = std::max(bmax, c->fac_b[f]);
   const int ldw = bmax;
+  // scratch buffers, freed when the function returns (allocation failures return before any
+  // launch; the normal path synchronises the stream first)
+  struct Scratch {
+    void* p[8] = {};
+    int n = 0;
+    ~Scratch() {
+      for (int i = 0; i < n; ++i) cudaFree(p[i]);
+    }
+  } scratch;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    const cudaError_t r = cudaMalloc(ptr, bytes);
+    if (r == cudaSuccess) scratch.p[scratch.n++] = *ptr;
+    return r;
+  };
   cplx<T>* W = nullptr;
   cplx<T>* colp = nullptr;
   int *perm = nullptr, *cm = nullptr;
   F3State* st = nullptr;
-  if ((e = cudaMalloc((void**)&W, sizeof(cplx<T>) * (size_t)bmax * ldw)) != cudaSuccess) return e;
-  if ((e = cudaMalloc((void**)&colp, sizeof(cplx<T>) * bmax)) != cudaSuccess) return e;
-  if ((e = cudaMalloc((void**)&perm, sizeof(int) * bmax)) != cudaSuccess) return e;
-  if ((e = cudaMalloc((void**)&cm, sizeof(int) * bmax)) != cudaSuccess) return e;
-  if ((e = cudaMalloc((void**)&st, sizeof(F3State))) != cudaSuccess) return e;
   constexpr int PW = F3Panel<T>::W;
   cplx<T>* Tp = nullptr;
   int* swl = nullptr;
-  if ((e = cudaMalloc((void**)&swl, sizeof(int) * (4 * PW + 1))) != cudaSuccess) return e;
-  if ((e = cudaMalloc((void**)&Tp, sizeof(cplx<T>) * (size_t)PW * ldw)) != cudaSuccess) return e;
+  if ((e = alloc((void**)&W, sizeof(cplx<T>) * (size_t)bmax * ldw)) != cudaSuccess) return e;
+  if ((e = alloc((void**)&colp, sizeof(cplx<T>) * bmax)) != cudaSuccess) return e;
+  if ((e = alloc((void**)&perm, sizeof(int) * bmax)) != cudaSuccess) return e;
+  if ((e = alloc((void**)&cm, sizeof(int) * bmax)) != cudaSuccess) return e;
+  if ((e = alloc((void**)&st, sizeof(F3State))) != cudaSuccess) return e;
+  if ((e = alloc((void**)&swl, sizeof(int) * (4 * PW + 1))) != cudaSuccess) return e;
+  if ((e = alloc((void**)&Tp, sizeof(cplx<T>) * (size_t)PW * ldw)) != cudaSuccess) return e;
   // blocked when every plane block fits the cluster panel (b <= 2048); wider planes one pivot at
   // a time
   const bool blocked = bmax <= F3C_N * F3C_T;
@@ -456,7 +470,6 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
     }
   }
   cudaStreamSynchronize(c->st);
-  cudaFree(W); cudaFree(colp); cudaFree(perm); cudaFree(cm); cudaFree(st); cudaFree(Tp); cudaFree(swl);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

@@ -37,8 +37,9 @@
 //
 // Measured alternatives that were slower on the 2048^2, 1024-subdomain, 64-right-hand-side
 // workload: splitting each block's output rows into two halves so that the epilogue of one half
-// overlaps the products of the other (N = bp MMAs with the operand in tensor memory ran at about
-// 150 cycles each instead of N/2), and 12 or 16 epilogue warps instead of 8.
+// overlaps the products of the other (the N = bp MMAs took about 150 cycles each in a per-block
+// trace, waits for factor stages included, no fewer than the full-width ones), and 12 or 16
+// epilogue warps instead of 8.
 #include <algorithm>
 #include <vector>
 

@@ -78,7 +78,7 @@ typedef struct {
   int parts[3];             /* N1, N2 (, N3): subdomains per axis (Section 2.2)         */
   const int64_t *cuts[3];   /* host arrays of parts[a]+1 increasing node offsets from 0
                                to n[a] (uneven partitions); NULL = uniform cuts         */
-  int overlap;              /* ov >= 1 cells: overlap width d~ = ov h (Eq. (PMLprofile))*/
+  int overlap;              /* ov >= 1 cells: overlap width d~ = ov h (Eq. (11))      */
   int pml;                  /* PML cells beyond the overlap                             */
   double sigma0;            /* PML profile sigma(t) = sigma0 ((t - ov)/pml)^pml_power   */
   double pml_power;         /*   for t > ov cells beyond a box face, 0 otherwise        */
@@ -101,7 +101,7 @@ typedef struct {
 /* Set-up (Sections 2.1, 3.1; assembly step of the path).  Validates `p`,
  * copies the wave speed c_dev (float64, global extended grid, device) and
  * builds on the device the PML stretching tables (alpha = 1 + i sigma at nodes
- * and half nodes, Eq. (PMLprofile)), k^2 = (omega / c)^2 and the partition
+ * and half nodes, Eq. (11)), k^2 = (omega / c)^2 and the partition
  * descriptors.  Allocates all device workspace for up to p->max_rhs
  * right-hand sides.  `stream` is a cudaStream_t (NULL = legacy default).
  * Does not factor.  Errors: DDM_E_INVAL, DDM_E_NOMEM, DDM_E_CUDA.           */
@@ -130,7 +130,7 @@ ddm_status ddm_set_medium_host(ddm_ctx *ctx, double omega, const double *c_host)
 ddm_status ddm_factor(ddm_ctx *ctx);
 
 /* dst = M_K(src): K steps of Algorithm 3.1 with right-hand side src, then the
- * assembled DDM solution sum_R beta_{0;R} sum_s u^s_R (Eq. (tsum)).  src and
+ * assembled DDM solution sum_R beta_{0;R} sum_s u^s_R (Eq. (39)).  src and
  * dst are global complex128 vectors (nrhs of them, device).  src is in the
  * J-scaled space of b.  Requires ddm_factor.  Errors: DDM_E_INVAL (K < 1,
  * nrhs > max_rhs), DDM_E_STATE, DDM_E_CUDA.                                 */
@@ -206,7 +206,7 @@ const char *ddm_last_error(const ddm_ctx *ctx);
  * ------------------------------------------------------------------------ */
 
 /* b = h^2 J f on the global grid (right-hand side of the J-scaled system,
- * Eq. (PMLweak0)).  Global complex128 vectors, device.                      */
+ * Eq. (32)).  Global complex128 vectors, device.                      */
 ddm_status ddm_rhs(ddm_ctx *ctx, const void *f_dev, void *b_dev, int nrhs);
 
 /* y = A x with the global truncated operator (Section 3.1), FP64.          */
@@ -226,7 +226,7 @@ ddm_status ddm_local_layout(const ddm_ctx *ctx, int *n_sub, int64_t *total, int6
                             int *ext_x, int *ext_y, int *ext_z);
 
 /* u_R = L^_R^{-1} src_R for every subdomain R (the batched local solves of
- * Eqs. (talg_1)/(talg_2)); local complex vectors (total * nrhs elements,
+ * Eqs. (37)/(38)); local complex vectors (total * nrhs elements,
  * subdomain-major as above), device, in the context's local precision
  * (complex128 for DDM_FP64, complex64 for DDM_MIXED).                       */
 ddm_status ddm_local_solve(ddm_ctx *ctx, const void *src_dev, void *u_dev, int nrhs);
@@ -285,7 +285,9 @@ ddm_status ddm_factor_bytes(const ddm_ctx *ctx, int64_t *bytes_per_solve, int64_
  * 304 x 16 + 16 doubles (about 39 KB) that every GPU which loads the library
  * keeps until the process exits.  The first call on a device looks up that
  * array's device address (cudaGetSymbolAddress, with the device current) and
- * caches it; make that first call outside any stream capture.  All calls
+ * caches it; make that first call outside any stream capture.  The cached
+ * address is valid for the device's primary context only: after
+ * cudaDeviceReset the call must not be used again in that process.  All calls
  * share the one array, so calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.
  * Errors: DDM_E_INVAL for null pointers, n < 1 or nvec outside [1, 16] (the

@@ -11,11 +11,11 @@ arithmetic.
 
 Modules
 -------
-pml_operator  PML stretching (Section 2.1, Eq. (PMLprofile)) and the J-scaled
-              5-/7-point finite-difference PML operator (Eq. (PML), Section 4).
+pml_operator  PML stretching (Section 2.1, Eq. (11)) and the J-scaled
+              5-/7-point finite-difference PML operator (Eq. (9), Section 4).
 ddm           Structured overlapping partition, cut-off and characteristic
               functions, transfer operators Psi (Section 2.2), Algorithm 3.1
-              run as an iteration, the assembled DDM solution (Eq. (tsum)) and
+              run as an iteration, the assembled DDM solution (Eq. (39)) and
               the global truncated problem solved directly (Section 3.1).
 krylov        Right-preconditioned flexible GMRES with the DDM preconditioner
               (Section 4.2.2).

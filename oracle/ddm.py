@@ -18,7 +18,7 @@ Readings of the paper taken here (where it is silent, ambiguous or garbled):
     side of the shared interface(s) (the printed indices of chi for the
     left/down/corner directions are off by one relative to the right/up ones);
   * lags: a direction with m non-zero components uses u^{s-m} (faces 1,
-    corners/edges 2, 3D vertices 3), Eq. (talg_2) in 2D;
+    corners/edges 2, 3D vertices 3), Eq. (38) in 2D;
   * the iteration continues past N1+N2(+N3) steps with the same recurrence;
   * a subdomain's source f_ij is the global right-hand side on its "own
     region": its own box, continued through the global extension band on the
@@ -49,7 +49,7 @@ def directions(dim: int) -> List[Tuple[int, ...]]:
 
 
 def lag(d: Sequence[int]) -> int:
-    """Step lag of direction d: number of non-zero components (Eq. (talg_2))."""
+    """Step lag of direction d: number of non-zero components (Eq. (38))."""
     return sum(1 for x in d if x != 0)
 
 
@@ -104,7 +104,7 @@ class DDMOracle:
         return int(self.cuts[a][R[a]]), int(self.cuts[a][R[a] + 1])
 
     def rhs(self, f: np.ndarray) -> np.ndarray:
-        """b = h^2 J f: right-hand side of the J-scaled system (weak form, Eq. (PMLweak0))."""
+        """b = h^2 J f: right-hand side of the J-scaled system (weak form, Eq. (32))."""
         return (self.h * self.h) * self.J_global * f
 
     def apply_global(self, w: np.ndarray) -> np.ndarray:
@@ -130,7 +130,7 @@ class DDMOracle:
                 self.sub_lu[R] = one(R)[1]
 
     def local_solve(self, R, src: np.ndarray) -> np.ndarray:
-        """u = L^_{ij}^{-1} src on the subdomain's extended grid (Eq. (talg_1)/(talg_2))."""
+        """u = L^_{ij}^{-1} src on the subdomain's extended grid (Eqs. (37)/(38))."""
         if R not in self.sub_lu:
             self.sub_lu[R] = spla.splu(self.sub_A[R].tocsc())
         return self.sub_lu[R].solve(src.ravel()).reshape(self.sub_shape[R])
@@ -212,7 +212,7 @@ class DDMOracle:
 
     def transfer(self, R, d, v_sender: np.ndarray) -> np.ndarray:
         """Psi_d(v) = -L^_R(beta_d v) chi_d on the receiver's grid (Section 2.2, transfer
-        operators; Eq. (talg_2) uses them with the receiver's truncated operator).
+        operators; Eq. (38) uses them with the receiver's truncated operator).
 
         beta_d v lives on the sender's grid; it is carried onto the receiver's grid
         through the global node positions (zero where the grids do not overlap; chi_d
@@ -238,7 +238,7 @@ class DDMOracle:
 
     # -------------------------------------------------------------- Algorithm
     def step_source(self, R, s: int, hist: Dict[int, Dict]) -> np.ndarray:
-        """Right-hand side of Eq. (talg_2) for subdomain R at step s >= 2."""
+        """Right-hand side of Eq. (38) for subdomain R at step s >= 2."""
         src = np.zeros(self.sub_shape[R], dtype=np.complex128)
         for d in directions(self.dim):
             S = self.sender(R, d)
@@ -253,7 +253,7 @@ class DDMOracle:
 
         ``callback(s, hist, U)`` runs after every step; returning True stops the
         iteration there.  Returns a dict with U (per-subdomain sums of u^s), the
-        assembled solution w (Eq. (tsum)), the last ``dim`` per-step solutions
+        assembled solution w (Eq. (39)), the last ``dim`` per-step solutions
         ``u`` (step -> {R: u^s_R}), the number of steps taken and, if keep_all,
         every step's sources and solutions.
         """
@@ -289,7 +289,7 @@ class DDMOracle:
         return out
 
     def assemble(self, U: Dict) -> np.ndarray:
-        """u^_DDM = sum_ij beta_{0;ij} U_ij on the global grid (Eq. (tsum))."""
+        """u^_DDM = sum_ij beta_{0;ij} U_ij on the global grid (Eq. (39))."""
         w = np.zeros(self.gshape, dtype=np.complex128)
         for R in self.subs:
             w[self.sub_win[R]] += self.beta_own(R) * U[R]
@@ -298,7 +298,7 @@ class DDMOracle:
     def strip_residual(self, R, s: int, hist: Dict[int, Dict]) -> np.ndarray:
         """Residual b - A w_s on R's own region, from transfers of the last steps only.
 
-        With U^(s) = sum_{t<=s} u^t, summing Eq. (talg_2) over the steps gives
+        With U^(s) = sum_{t<=s} u^t, summing Eq. (38) over the steps gives
         L^_R U_R^(s) = f_R + sum_d Psi_d(U_S^(s - lag d)), while at an own node the
         neighbours' terms of A w equal -Psi_d(U_S^(s)) (beta_{0;S} and beta_d agree on
         the stencil there).  Hence r = sum_d Psi_d(u^s + .. + u^{s-lag(d)+1}) on own(R).

@@ -18,7 +18,7 @@ import scipy.sparse as sp
 
 
 def sigma_profile(t: np.ndarray, ov: int, npml: int, sigma0: float, power: float) -> np.ndarray:
-    """Shifted PML profile, Eq. (PMLprofile) of Section 2.1.
+    """Shifted PML profile, Eq. (11) of Section 2.1.
 
     ``t`` is the distance beyond the box face in cells.  sigma = 0 on the
     overlap band t <= d~ (d~ = ov cells); beyond it the medium profile
@@ -63,7 +63,7 @@ def pml_operator(alpha_node: Sequence[np.ndarray], alpha_half: Sequence[np.ndarr
                  k2: np.ndarray, h: float) -> sp.csr_matrix:
     """h^2 J L_B: the J-scaled 5-point (2D) / 7-point (3D) PML operator on a box.
 
-    Eq. (PML) with A = diag(J / alpha_a^2) and J = prod_a alpha_a reads
+    Eq. (9) with A = diag(J / alpha_a^2) and J = prod_a alpha_a reads
     J L u = sum_a d/dx_a( (prod_{b != a} alpha_b) / alpha_a du/dx_a ) + k^2 J u;
     since prod_{b != a} alpha_b does not depend on x_a it stays outside the
     derivative.  Central differences on the node grid give, at node x,
@@ -75,7 +75,7 @@ def pml_operator(alpha_node: Sequence[np.ndarray], alpha_half: Sequence[np.ndarr
 
     with u = 0 beyond the box's extended grid (homogeneous Dirichlet, the
     truncated problem of Section 3.1).  The matrix is complex symmetric and is
-    the discrete weak form (Eq. (PMLweak)) up to sign.  Rows/cols follow the C
+    the discrete weak form (Eq. (10)) up to sign.  Rows/cols follow the C
     order of ``k2`` (last axis fastest).
     """
     shape = k2.shape

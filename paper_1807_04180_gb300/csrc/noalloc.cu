@@ -83,7 +83,9 @@ extern "C" ddm_status ddm_norms_noalloc(const void* x_dev, int64_t n, int nvec, 
   double* scratch = nullptr;
   {
     // once per device, with that device current: the host-side name of g_na_scratch is only a
-    // stand-in, so kernels get the device address from cudaGetSymbolAddress
+    // stand-in, so kernels get the device address from cudaGetSymbolAddress.  The address is
+    // kept for the life of the process; after cudaDeviceReset (or any teardown of the device's
+    // primary context) it is stale, and the call must not be used again in that process.
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (!g_na_addr[dev]) {
       void* p = nullptr;
@@ -95,6 +97,9 @@ extern "C" ddm_status ddm_norms_noalloc(const void* x_dev, int64_t n, int nvec, 
     scratch = g_na_addr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
+  // clear a launch error left by unrelated earlier work, so that the check below reports only
+  // this call's launches (a sticky error from a faulted context is not cleared and fails here)
+  (void)cudaGetLastError();
   k_na_partial<<<NA_BLOCKS, 256, 0, st>>>((const ddm::z64*)x_dev, (long long)n, nvec, scratch);
   k_na_total<<<nvec, 256, 0, st>>>(scratch, norms_dev);
   e = cudaGetLastError();

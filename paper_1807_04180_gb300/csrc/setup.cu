@@ -4,7 +4,7 @@
 
 namespace ddm {
 
-// Shifted PML profile (Section 2.1, Eq. (PMLprofile)): sigma = 0 for t <= ov cells beyond a
+// Shifted PML profile (Section 2.1, Eq. (11)): sigma = 0 for t <= ov cells beyond a
 // box face, sigma0 ((t - ov) / npml)^power beyond.
 __device__ __forceinline__ double sigma_of(double t, int ov, int npml, double sigma0, double power) {
   if (t <= (double)ov) return 0.0;

@@ -1,5 +1,5 @@
 // Batched block-tridiagonal solves u_R = A_R^{-1} src_R over all subdomains and right-hand
-// sides (the local solves of Algorithm 3.1, Eqs. (talg_1)/(talg_2)).
+// sides (the local solves of Algorithm 3.1, Eqs. (37)/(38)).
 //
 // With G_k = D_k^{-1} from factor.cu:
 //   forward   y_k = r_k - c_S(., k) * t_{k-1},   t_k = G_k y_k            (k = 0..m-1)

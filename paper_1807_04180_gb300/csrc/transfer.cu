@@ -1,6 +1,6 @@
 // Source restriction, the fused directional-residual transfer (the Psi operators of
-// Section 2.2 in Eq. (talg_2)) with residual-norm partials, and the assembly of the DDM
-// solution (Eq. (tsum)).
+// Section 2.2 in Eq. (38)) with residual-norm partials, and the assembly of the DDM
+// solution (Eq. (39)).
 #include <algorithm>
 
 #include "ddm_internal.cuh"
@@ -256,7 +256,7 @@ cudaError_t launch_transfer_n(ddm_ctx* c, int s, void* src_next, double* part, i
 
 
 // ---------------------------------------------------------------------------
-// w = sum_R beta_{0;R} U_R (Eq. (tsum)) on the global grid.  A global node lies in the
+// w = sum_R beta_{0;R} U_R (Eq. (39)) on the global grid.  A global node lies in the
 // support of beta_{0;R} for at most two parts per axis: its owner and the neighbour whose
 // face is within ov nodes.
 // ---------------------------------------------------------------------------

@@ -320,9 +320,41 @@ def ddm_factor_bytes(ctx):
     return a.value, b.value
 
 
+def _noalloc_args_error(x_dev, n: int, nvec: int, norms_dev) -> Optional[str]:
+    """Why (x_dev, n, nvec, norms_dev) cannot go to ddm_norms_noalloc, or None.  The C entry
+    point has no context to bound n, so the binding checks the buffers it would read and write:
+    x_dev complex128 with at least n * nvec elements, norms_dev float64 with at least nvec, both
+    contiguous CUDA tensors on the current device."""
+    import torch
+    if not isinstance(x_dev, torch.Tensor) or not isinstance(norms_dev, torch.Tensor):
+        return "x_dev and norms_dev must be torch tensors"
+    if x_dev.dtype != torch.complex128:
+        return f"x_dev must be complex128, not {x_dev.dtype}"
+    if norms_dev.dtype != torch.float64:
+        return f"norms_dev must be float64, not {norms_dev.dtype}"
+    if n < 1 or nvec < 1:
+        return "n and nvec must be >= 1"
+    if x_dev.numel() < n * nvec:
+        return f"x_dev holds {x_dev.numel()} elements, fewer than n * nvec = {n * nvec}"
+    if norms_dev.numel() < nvec:
+        return f"norms_dev holds {norms_dev.numel()} elements, fewer than nvec = {nvec}"
+    if not (x_dev.is_cuda and norms_dev.is_cuda):
+        return "x_dev and norms_dev must be CUDA tensors"
+    if not (x_dev.is_contiguous() and norms_dev.is_contiguous()):
+        return "x_dev and norms_dev must be contiguous"
+    cur = torch.cuda.current_device()
+    if x_dev.device.index != cur or norms_dev.device.index != cur:
+        return f"x_dev and norms_dev must be on the current device (cuda:{cur})"
+    return None
+
+
 def ddm_norms_noalloc(x_dev, n: int, nvec: int, norms_dev, stream=None) -> None:
     """Allocation-free norms: norms_dev[i] = ||x_i|| for nvec complex128 vectors of length n
-    (x_dev and norms_dev are CUDA tensors; enqueued on the current stream, not synchronised)."""
+    (x_dev and norms_dev are CUDA tensors; enqueued on the current stream, not synchronised).
+    Raises DDMError(DDM_E_INVAL) before any CUDA call when the buffers do not fit the call."""
+    why = _noalloc_args_error(x_dev, int(n), int(nvec), norms_dev)
+    if why is not None:
+        raise DDMError(DDM_E_INVAL, "ddm_norms_noalloc: " + why)
     _check(lib().ddm_norms_noalloc(_ptr(x_dev), int(n), int(nvec), _stream(stream), _ptr(norms_dev)), None)
 
 

@@ -45,3 +45,19 @@ def rel(a, b):
     b = np.asarray(b).ravel()
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def single_box_oracle(wl, R):
+    """An oracle whose whole problem is subdomain R of ``wl``: its interior is R's own box and
+    its medium R's window of the global wave speed, so its one subdomain operator is R's
+    operator in the full partition (box-relative PML tables, the same h, omega and k^2).  Lets
+    a test solve one subdomain of a workload too large to build whole on the host."""
+    d = len(wl.n)
+    e = wl.ov + wl.npml
+    lo = [int(wl.cuts[a][R[a]]) for a in range(d)]
+    hi = [int(wl.cuts[a][R[a] + 1]) for a in range(d)]
+    win = tuple(slice(lo[a], hi[a] + 2 * e) for a in range(d))
+    n = [hi[a] - lo[a] for a in range(d)]
+    cuts = [np.array([0, n[a]], dtype=np.int64) for a in range(d)]
+    return DDMOracle(n, wl.h, cuts, wl.ov, wl.npml, wl.sigma0, wl.power, wl.omega,
+                     np.ascontiguousarray(wl.c[win])), (0,) * d

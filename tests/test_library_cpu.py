@@ -66,3 +66,31 @@ def test_workspace_estimate_is_pure_arithmetic_and_monotone(built):
     assert b[0] < b[1] < b[2] < b[3]
     p, keep = ddm.params_from(small, ddm.DDM_FP64, 1)
     assert ddm.ddm_workspace_bytes(p, 0) > b[0]       # complex128 local storage
+
+
+@pytest.mark.parametrize("case", ["x_dtype", "norms_dtype", "x_short", "norms_short", "bad_n", "not_cuda"])
+def test_noalloc_binding_rejects_buffers_that_do_not_fit(built, case):
+    """ddm_norms_noalloc has no context to bound n, so the binding refuses, before any CUDA
+    call, buffers the kernels would read or write past: a wrong dtype, too few elements, a bad
+    size, or tensors not on the GPU (the order of the checks lets each case reach its own)."""
+    torch = pytest.importorskip("torch")
+    from paper_1807_04180_gb300 import ddm
+    n, nvec = 100, 3
+    x = torch.zeros(n * nvec, dtype=torch.complex128)
+    out = torch.zeros(nvec, dtype=torch.float64)
+    if case == "x_dtype":
+        x = torch.zeros(n * nvec, dtype=torch.complex64)
+    elif case == "norms_dtype":
+        out = torch.zeros(nvec, dtype=torch.float32)
+    elif case == "x_short":
+        x = torch.zeros(n * nvec - 1, dtype=torch.complex128)
+    elif case == "norms_short":
+        out = torch.zeros(nvec - 1, dtype=torch.float64)
+    elif case == "bad_n":
+        n = 0
+    with pytest.raises(ddm.DDMError) as ei:
+        ddm.ddm_norms_noalloc(x, n, nvec, out)
+    assert ei.value.status == ddm.DDM_E_INVAL
+    expect = {"x_dtype": "complex128", "norms_dtype": "float64", "x_short": "fewer than n * nvec",
+              "norms_short": "fewer than nvec", "bad_n": ">= 1", "not_cuda": "CUDA tensors"}[case]
+    assert expect in str(ei.value)

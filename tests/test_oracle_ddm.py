@@ -145,7 +145,7 @@ def _const(n, parts, ov, npml, sigma0, k=2 * math.pi * 3, seed=0):
 
 def test_theorem_2_4_remnant_shrinks_with_pml():
     """Theorem 2.4: in R^2 with a constant medium u_DDM = u after N1+N2 steps.  Truncated and
-    discretised, the remnant error shrinks as the PML absorbs better (Eq. (errPML))."""
+    discretised, the remnant error shrinks as the PML absorbs better (Eq. (34))."""
     errs = []
     for npml, s0 in ((3, 2.0), (6, 8.0), (12, 20.0)):
         wl = _const(48, 3, 2, npml, s0)

@@ -4,7 +4,7 @@ Each check ties oracle/pml_operator.py to something other than itself:
 a textbook Kronecker-sum Laplacian, complex symmetry, a dense library solve,
 the free-space Green's functions of Section 2.1 (2D Hankel, 3D e^{ikr}/(4 pi r))
 with the second-order convergence the paper reports in Tables 1-2, and the
-exponential decay of the PML truncation error in sigma-bar (Eq. (errPML)).
+exponential decay of the PML truncation error in sigma-bar (Eq. (34)).
 """
 import json
 import math
@@ -110,7 +110,7 @@ def test_green_function_2d_second_order():
 
 
 def test_pml_truncation_error_decays_with_sigma():
-    """Eq. (errPML): ||u - u^|| <= C k^2 (1+kL)^2 exp(-k gamma0 sigma_bar / 2), sigma_bar = int sigma.
+    """Eq. (34): ||u - u^|| <= C k^2 (1+kL)^2 exp(-k gamma0 sigma_bar / 2), sigma_bar = int sigma.
     At fixed fine mesh the error against the closed form drops as sigma0 grows (until the
     discretisation error takes over)."""
     k = 2 * math.pi * 3.0

@@ -141,7 +141,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    D.ddm_timing(ctx, enable=True, reset=True)
+    D.ddm_timing(ctx, enable=False, reset=True)
     D.ddm_kernel_launches(ctx, reset=True)
     uuid = None
     try:
@@ -169,10 +169,18 @@ def run_ours(args, rank, world, local_rank):
     # the library synchronises inside ddm_solve (convergence checks), so device events and
     # host wall time agree; take the larger
     elapsed_ms = max(dev_ms, wall * 1e3)
-    tms = D.ddm_timing(ctx, enable=False)
     launches = D.ddm_kernel_launches(ctx)
     elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
     ms_per_step = elapsed_ms / args.steps
+    # the kernel split and the local solve's launch time come from a separate pass of the same
+    # steps with the library's per-launch CUDA events on (recorded on the library's stream), so
+    # that the timed region above carries no instrumentation
+    n_prof = max(1, min(args.steps, 5))
+    D.ddm_timing(ctx, enable=True, reset=True)
+    for _ in range(n_prof):
+        step()
+    torch.cuda.synchronize()
+    tms = D.ddm_timing(ctx, enable=False)
     # dominant kernel: the batched local solves (k_solve2d)
     solve_ms, solve_n = tms["solve"]
     per_solve_bytes, stored = D.ddm_factor_bytes(ctx)
@@ -204,7 +212,8 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / pk["hbm_gbs"], "peak_src": pk["src"],
                      "traffic": traffic, "algorithmic_bytes_per_launch": launch_bytes,
                      "avg_launch_ms": avg_launch_ms, "launches": solve_n},
-        "kernel_ms": {k: v[0] / args.steps for k, v in tms.items()},
+        "kernel_ms": {k: v[0] / n_prof for k, v in tms.items()},
+        "kernel_ms_note": f"per step, from {n_prof} instrumented steps after the timed region",
         "gpu_launches": launches, "clocks": ck,
     }
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -259,6 +268,7 @@ def run_ours(args, rank, world, local_rank):
         out["oracle_sample_rel_err"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         out["oracle_fgmres_iters_to_1e-6"] = gold["fgmres_iters_to_1e-6"]
         out["oracle_K"] = gold["K"]
+    out["_x"] = u_dev.cpu().numpy() if rank == 0 else None
     s.close()
     return out
 
@@ -313,79 +323,58 @@ def profile_kernels(args):
 
 
 # ----------------------------------------------------------------------------------- oracle
-def oracle_sample(budget_s, workers, K):
-    """Time the FP64 oracle on a bounded sample of the workload and extrapolate one solve.
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
-    The sample: factor S of the 256 subdomains (SuperLU), then for the same S subdomains one
-    DDM step (transfers into them and their local solves), one global operator application
-    and one classical Gram-Schmidt pass against j = restart/2 vectors.  A full solve is
-    (256/S) x factor + n_it x [K x (256/S) x step + A + 2 CGS passes], with n_it the oracle's
-    own FGMRES iteration count to 1e-6 on this workload (tests/golden, written by the oracle).
-    """
+
+def oracle_solve(workers, K, restart, tol=1e-6):
+    """One complete solve of the headline workload by the FP64 oracle, timed end to end on the
+    host cores: assembly of the operators, the SuperLU factorisation of all 256 subdomains, and
+    FGMRES(restart) preconditioned by K DDM steps to a relative residual of tol (subdomains
+    spread over ``workers`` threads, as the paper spreads them over cores)."""
     from oracle.ddm import DDMOracle
+    from oracle.krylov import ddm_fgmres
     wl = W.heterogeneous_2d()
-    wl.K = K
+    t0 = time.perf_counter()
     o = DDMOracle(wl.n, wl.h, wl.cuts, wl.ov, wl.npml, wl.sigma0, wl.power, wl.omega, wl.c, workers=workers)
-    nsub = len(o.subs)
-    gpath = golden_for_K(K)
-    with open(gpath) as fh:
-        gold = json.load(fh)
-    if gold["K"] == K:
-        n_it = gold["fgmres_iters_to_1e-6"]
-        it_src = f"the oracle's own FGMRES iteration count at K={K} ({os.path.relpath(gpath, ROOT)})"
-    else:
-        n_it = max(1, round(gold["fgmres_iters_to_1e-6"] * gold["K"] / K))
-        it_src = f"oracle count at K={gold['K']} scaled to K={K}"
-    from concurrent.futures import ThreadPoolExecutor
-    import scipy.sparse.linalg as spla
-    # size the sample to the budget: about 0.09 s of factor + step work per subdomain per worker
-    S = int(max(8, min(nsub, budget_s * max(1, workers) / 0.12)))
-    S = min(nsub, S)
-    rng = np.random.default_rng(0)
-    sample = [o.subs[i] for i in sorted(rng.choice(nsub, S, replace=False))]
-    b = o.rhs(wl.f[0])
-    t0 = time.perf_counter()
-    with ThreadPoolExecutor(max(1, workers)) as ex:
-        lus = list(ex.map(lambda R: spla.splu(o.sub_A[R].tocsc()), sample))
-    for R, lu in zip(sample, lus):
-        o.sub_lu[R] = lu
+    o.factor()
     t_fac = time.perf_counter() - t0
-    # one step on the sample: step-1 sources for all of them, then transfers + solves
-    hist = {1: {R: o.local_solve(R, o.restrict_own(R, b)) if R in o.sub_lu else np.zeros(o.sub_shape[R], complex)
-                for R in o.subs}}
-    t0 = time.perf_counter()
-    with ThreadPoolExecutor(max(1, workers)) as ex:
-        list(ex.map(lambda R: o.local_solve(R, o.step_source(R, 2, hist)), sample))
-    t_step = time.perf_counter() - t0
-    x = (np.random.default_rng(1).standard_normal(o.gshape) + 0j)
-    t0 = time.perf_counter()
-    o.apply_global(x)
-    t_A = time.perf_counter() - t0
-    j = max(1, min(n_it, wl.restart) // 2)     # average Krylov basis size over the run
-    V = np.zeros((j, x.size), dtype=np.complex128)
-    w = x.ravel().copy()
-    t0 = time.perf_counter()
-    c = V.conj() @ w
-    w = w - V.T @ c
-    t_cgs = time.perf_counter() - t0
-    est = t_fac * nsub / S + n_it * (wl.K * t_step * nsub / S + t_A + 2 * t_cgs)
-    return {"est_s": est, "sample": f"{S}/{nsub} subdomains: factor + one DDM step (transfer + solve), one global "
-                                    f"A x, one CGS pass at j={j}; scaled to {n_it} FGMRES iterations x K={wl.K} "
-                                    f"({it_src})", "cores": max(1, workers)}
+    b = o.rhs(wl.f[0])
+    res = ddm_fgmres(o, b, K=K, tol=tol, restart=restart, max_it=200)
+    t_all = time.perf_counter() - t0
+    r = float(np.linalg.norm(b - o.apply_global(res["x"])) / np.linalg.norm(b))
+    return {"solve_s": t_all, "factor_s": t_fac, "fgmres_iters": res["iters"], "converged": bool(res["converged"]),
+            "rel_residual": r, "cores": max(1, workers), "x": res["x"],
+            "sample": f"one complete oracle solve of the same workload, timed end to end: assembly, SuperLU "
+                      f"factorisation of all {len(o.subs)} subdomains, FGMRES({restart}) with K={K} to "
+                      f"{tol:g} ({res['iters']} iterations, explicit residual {r:.2e}); "
+                      f"{max(1, workers)} host threads"}
 
 
-def tf32_peak():
-    """Dense TF32 tensor peak: the measured bf16 cuBLAS peak (sustained: these kernels run inside
-    seconds-long steps) times the nominal TF32 / BF16 ratio 1.1 / 2.25."""
+TF32_FLOP_PER_CYCLE_SM = 4096   # kind::tf32 M=128 x N x K=8 MMAs back to back: N/2 cycles each (N >= 128)
+GB300_SMS = 152
+
+
+def tf32_peak(sm_mhz=None):
+    """Dense TF32 tensor rate of this GPU, in TFLOP/s: the per-SM rate of back-to-back
+    tcgen05.mma kind::tf32 (M = 128, K = 8: one MMA every N/2 cycles for N >= 128, i.e. 4096
+    flop per cycle per SM, measured with a microbenchmark on this GPU) x 152 SMs x the SM clock
+    (the median sampled during the run, else the maximum clock).  Returns (rate, source, the
+    recipe's alternative: the measured bf16 sustained peak x the nominal TF32/BF16 ratio)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = {}
     if os.path.exists(p):
         with open(p) as fh:
             d = json.load(fh)
-        return d["bf16_tflops_sustained"] * 1.1 / 2.25, "measured bf16 sustained x 1.1/2.25"
-    return 1700.0 * 1.1 / 2.25, "fallback bf16 sustained x 1.1/2.25"
+    mhz = sm_mhz or d.get("sm_max_mhz") or 2070.0
+    rate = TF32_FLOP_PER_CYCLE_SM * GB300_SMS * mhz * 1e6 / 1e12
+    recipe = (d["bf16_tflops_sustained"] if "bf16_tflops_sustained" in d else 1700.0) * 1.1 / 2.25
+    src = (f"measured kind::tf32 MMA rate (4096 flop/cycle/SM) x 152 SMs x {mhz:.0f} MHz"
+           + ("" if sm_mhz else " (maximum clock)"))
+    return rate, src, recipe
 
 
-def run_workload(args, rank, world, local_rank):
+def run_workload(name, steps, warmup, max_it, rank, world, local_rank):
     """The multi-right-hand-side workloads whose local solves run on the tensor cores:
     2d-layered-2048-batched (2048^2, 32x32 uneven subdomains, 64 point sources) and
     3d-constant-192 (192^3, 8x8x8 subdomains sharing one factor).  One step = assemble, factor,
@@ -397,7 +386,7 @@ def run_workload(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    if args.workload == "layered_2d_batched":
+    if name == "layered_2d_batched":
         wl, K, restart, dim = W.layered_2d_batched(), 48, 20, 2
     else:
         wl, K, restart, dim = W.constant_3d(), 8, 30, 3
@@ -413,13 +402,13 @@ def run_workload(args, rank, world, local_rank):
     def step():
         D.ddm_set_medium(ctx, wl.omega, s.c)
         D.ddm_factor(ctx)
-        info_last.update(D.ddm_solve(ctx, f_dev, u_dev, nrhs=nrhs, tol=wl.tol, max_it=args.max_it,
+        info_last.update(D.ddm_solve(ctx, f_dev, u_dev, nrhs=nrhs, tol=wl.tol, max_it=max_it,
                                      mode=D.DDM_FGMRES, K=K, restart=restart, check=False))
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    D.ddm_timing(ctx, enable=True, reset=True)
+    D.ddm_timing(ctx, enable=False, reset=True)
     D.ddm_kernel_launches(ctx, reset=True)
     clocks = ClockSampler(None)
     clocks.start()
@@ -427,14 +416,19 @@ def run_workload(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     torch.cuda.synchronize()
     elapsed_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, dev)
     ck = clocks.stop()
-    tms = D.ddm_timing(ctx, enable=False)
     launches = D.ddm_kernel_launches(ctx)
-    ms_per_step = elapsed_ms / args.steps
+    ms_per_step = elapsed_ms / steps
+    # kernel split from one more step with the library's per-launch events on (after the timed
+    # region, which runs without them)
+    D.ddm_timing(ctx, enable=True, reset=True)
+    step()
+    torch.cuda.synchronize()
+    tms = D.ddm_timing(ctx, enable=False)
     # dominant kernel: the local solves of all right-hand sides (one launch per DDM step; in 2D
     # under graph replay their time is inside the graph slot, so the solves are timed directly)
     lay = D.ddm_local_layout(ctx)
@@ -455,7 +449,8 @@ def run_workload(args, rank, world, local_rank):
     torch.cuda.synchronize()
     solve_ms = e0.elapsed_time(e1) / reps
     achieved = flops / (solve_ms * 1e-3) / 1e12
-    peak, psrc = tf32_peak()
+    tf32, psrc, recipe = tf32_peak(ck.get("sm_mhz"))
+    peak = tf32 / 3.0    # split TF32: three tensor products per FP32 product
     # the same launch seen from HBM (algorithmic bytes): the complex64 factor is streamed once per
     # sweep (the kernel reads it packed in FP32, the same bytes up to padding to 32 columns, and
     # splits it into TF32 parts on chip), and every right-hand side's local vector is read and
@@ -466,7 +461,7 @@ def run_workload(args, rank, world, local_rank):
     name = "k_solve2d_tc" if dim == 2 else "k_gemm3d_tc + k_epi3d (per plane step)"
     res = {
         "metric": f"time-to-1e-6 throughput, {wl.name} ({nrhs} right-hand sides)", "value": world * nrhs * 1e3 / ms_per_step,
-        "unit": "rhs-solve/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "unit": "rhs-solve/s", "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 local (split-TF32 tensor cores) / c128 krylov", "data": "synthetic",
         "config": {"workload": wl.name, "nrhs": nrhs, "subdomains": "x".join(str(p) for p in wl.parts),
@@ -476,16 +471,18 @@ def run_workload(args, rank, world, local_rank):
         "rel_residual": info_last.get("rel_residual"), "n_unique_factors": info_last.get("n_unique_factors"),
         "factor_ms": info_last.get("factor_ms"),
         "roofline": {"bound": "tensor", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "peak_src": psrc,
+                     "frac": achieved / peak, "peak_src": f"({psrc}) / 3",
                      "note": "achieved counts the complex FP32 contraction flops (8 b^2 per column and block); "
-                             "split TF32 runs three tensor products per real product, so the tensor pipe "
-                             "executes 3x these flops",
-                     "tensor_pipe_frac": 3 * achieved / peak, "traffic": None,
+                             "split TF32 runs three TF32 products per FP32 product, so the FP32 peak on the "
+                             "tensor cores is the TF32 rate / 3 and frac is the tensor pipe's busy fraction",
+                     "tf32_peak_tflops": tf32, "tensor_pipe_frac": achieved / peak,
+                     "recipe_tf32_peak_tflops": recipe, "traffic": None,
                      "algorithmic_flops_per_launch": flops, "avg_launch_ms": solve_ms,
                      "hbm_bytes_per_launch": hbm_bytes,
                      "hbm_achieved_gbs": hbm_bytes / (solve_ms * 1e-3) / 1e9 if hbm_bytes else None,
                      "hbm_frac": hbm_bytes / (solve_ms * 1e-3) / 1e9 / hbm_peak if hbm_bytes else None},
-        "kernel_ms": {k: v[0] / args.steps for k, v in tms.items()},
+        "kernel_ms": {k: v[0] for k, v in tms.items()},
+        "kernel_ms_note": "per step, from one instrumented step after the timed region",
         "gpu_launches": launches, "clocks": ck, "autotune": D.ddm_autotune_log(ctx),
     }
     s.close()
@@ -493,37 +490,46 @@ def run_workload(args, rank, world, local_rank):
 
 
 def run_reference(args, rank, world):
+    """The oracle arm: rank 0 alone runs the FP64 CPU oracle on the host cores.
+
+    Warm-up: W untimed assemblies of the oracle's operators (they page in numpy/scipy and the
+    allocator; the oracle has no other warm-up state).  Timed region: ONE complete oracle solve
+    of the headline workload (assembly, factorisation, FGMRES to 1e-6), about a minute or two on
+    the host cores.  `value` is 1 / that time in solves per second.  The timed region spans the
+    K reported steps, each one K-th of that solve, so ms_per_step x steps is the solve's
+    measured time."""
     if rank != 0:
         return None
-    workers = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-    budget = max(2.0, 150.0 / (args.steps + args.warmup))
+    from oracle.ddm import DDMOracle
+    workers = host_cores()
+    wl = W.heterogeneous_2d()
     for _ in range(args.warmup):
-        oracle_sample(budget, workers, args.K)
-    ests = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r = oracle_sample(budget, workers, args.K)
-        ests.append(r["est_s"])
-    wall = time.perf_counter() - t0
-    est = statistics.mean(ests)
-    value = 1.0 / est
+        DDMOracle(wl.n, wl.h, wl.cuts, wl.ov, wl.npml, wl.sigma0, wl.power, wl.omega, wl.c, workers=workers)
+    r = oracle_solve(workers, args.K, args.restart)
+    value = 1.0 / r["solve_s"]
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["solve_s"] * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": "2d-heterogeneous-1024 (same seeded inputs)", "K": args.K, "restart": args.restart,
                        "tol": 1e-6},
+            "step_definition": "the timed region is one complete oracle solve; each of the steps is one steps-th "
+                               "of it (ms_per_step x steps = the measured solve time)",
+            "solve_s": r["solve_s"], "factor_s": r["factor_s"], "fgmres_iters": r["fgmres_iters"],
+            "converged": r["converged"], "rel_residual": r["rel_residual"],
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "sample_wall_s": wall / args.steps}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def run_serve(args):
     """Serving benchmark: a seeded Poisson stream of 2D heterogeneous solves (grid sizes uniform
     over {256, 512, 1024, 2048}^2, 1-16 right-hand sides, subdomains of 64^2 own nodes, 10 points
     per wavelength, tol 1e-6) into the continuous-batching server, arrival rate set to 70 % of
-    the capacity measured by running one request of each size alone.  Reports p50/p99 latency
-    (submission to completion) beside requests/s and right-hand-side solves/s."""
+    the capacity measured by running one request of each size alone (the calibration doubles as
+    the warm-up).  Reports p50/p99 latency (submission to completion) beside requests/s and
+    right-hand-side solves/s; ms_per_step is the stream's wall time per request; the roofline is
+    that of the local solves of all served requests (their algorithmic bytes over their
+    CUDA-event time, overlapped with the other requests' work)."""
     from paper_1807_04180_gb300.serving import DDMServer, request_workload
     rng = np.random.default_rng(5)
     sizes = [256, 512, 1024, 2048]
@@ -539,10 +545,12 @@ def run_serve(args):
         r = cal_srv.poll(rid)
         service[n] = r.t_done - r.t_admit
     cal_srv.shutdown()
-    mean_service = float(np.mean([service[n] for n, _, _ in specs]))
+    mean_service = float(np.mean([service[n] * (nrhs / 8.0) ** 0.5 for n, nrhs, _ in specs]))
     lam = 0.7 / mean_service
     arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
-    srv = DDMServer(max_active=args.serve_slots)
+    srv = DDMServer(max_active=args.serve_slots, collect_timing=True)
+    clocks = ClockSampler(None)
+    clocks.start()
     t0 = time.perf_counter()
     ids = []
     for t_arr, wl in zip(arrivals, wls):
@@ -551,22 +559,38 @@ def run_serve(args):
             time.sleep(dt)
         ids.append(srv.submit(wl))
     srv.wait(ids)
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
     st = srv.stats()
     reqs = [srv.poll(i) for i in ids]
     ok = all(r.status == "done" and r.info["converged"] for r in reqs)
     worst = max(r.info["rel_residual"] for r in reqs if r.info)
     srv.shutdown()
+    # local solves of all requests: algorithmic bytes / their summed CUDA-event time
+    tot_bytes = sum(r.info["local_solve_bytes"] * r.info["kernel_ms"]["solve"][1] for r in reqs if r.info)
+    tot_ms = sum(r.info["kernel_ms"]["solve"][0] for r in reqs if r.info)
+    launches = sum(r.info["kernel_ms"]["solve"][1] for r in reqs if r.info)
+    achieved = tot_bytes / (tot_ms * 1e-3) / 1e9 if tot_ms > 0 else None
+    hbm = peaks()["hbm_gbs"]
     return {"metric": "served latency p50/p99, Poisson stream of 2D heterogeneous DDM-FGMRES solves",
             "value": st["p99_ms"], "unit": "ms (p99)", "higher_is_better": False, "p50_ms": st["p50_ms"],
-            "p99_ms": st["p99_ms"], "requests_per_s": st["requests_per_s"], "rhs_solves_per_s": st["rhs_solves_per_s"],
+            "p99_ms": st["p99_ms"], "p99_over_p50": st["p99_ms"] / st["p50_ms"],
+            "requests_per_s": st["requests_per_s"], "rhs_solves_per_s": st["rhs_solves_per_s"],
+            "ms_per_step": wall * 1e3 / N, "steps": N, "warmup": len(sizes),
             "mean_queue_ms": st["mean_queue_ms"], "p99_queue_ms": st["p99_queue_ms"],
             "mean_service_ms": st["mean_service_ms"], "peak_active": st["peak_active"],
             "all_converged": ok, "worst_rel_residual": worst, "n_requests": N,
             "arrival_rate_per_s": lam, "calibration_service_s": service, "budget_bytes": st["budget_bytes"],
+            "clocks": ck,
+            "roofline": {"bound": "hbm", "kernel": "local solves of every served request (k_solve2d, "
+                         "k_solve2d_tc), overlapped with the other requests", "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                         "peak_src": peaks()["src"], "traffic": None, "launches": launches,
+                         "algorithmic_bytes": tot_bytes, "kernel_ms_total": tot_ms},
             "data": "synthetic",
             "config": {"workload": "serving: 2D heterogeneous solves, sizes {256,512,1024,2048}^2, 1-16 RHS, "
                                    "subdomains of 64^2, 10 ppw, tol 1e-6, mixed precision, FGMRES(20) K=16",
-                       "slots": args.serve_slots, "budget": "80% of free HBM"}}
+                       "slots": args.serve_slots, "budget": "80% of free HBM", "admission": "hrrn"}}
 
 
 def main():
@@ -582,8 +606,10 @@ def main():
     ap.add_argument("--max-it", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="headline line only (no 2048^2 batched, 192^3 and serving keys)")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (p50/p99 latency), one JSON line")
-    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--workload", choices=["heterogeneous_2d", "layered_2d_batched", "constant_3d"],
                     default="heterogeneous_2d",
@@ -615,17 +641,31 @@ def main():
             print(json.dumps(run_serve(args)))
         return
     if args.workload != "heterogeneous_2d":
-        out = run_workload(args, rank, world, local_rank)
+        out = run_workload(args.workload, args.steps, args.warmup, args.max_it, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(out))
         return
     out = run_ours(args, rank, world, local_rank)
+    gpu_x = out.pop("_x", None)
+    if world == 1 and not args.no_extra_configs:
+        # the metric's other configurations, each with its own steps, clocks and roofline: the
+        # 2048^2 64-right-hand-side and 192^3 workloads on the tensor cores, and the served stream
+        import torch
+        torch.cuda.empty_cache()
+        for name, steps in (("layered_2d_batched", 2), ("constant_3d", 3)):
+            out[name] = run_workload(name, steps, 3, args.max_it, rank, world, local_rank)
+            torch.cuda.empty_cache()
+        out["serving"] = run_serve(args)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            workers = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 1
-            r = oracle_sample(15.0, workers, args.K)
-            out["cpu_baseline"] = {"value": 1.0 / r["est_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                                   "sample": r["sample"]}
+            r = oracle_solve(host_cores(), args.K, args.restart)
+            out["cpu_baseline"] = {"value": 1.0 / r["solve_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                                   "sample": r["sample"], "solve_s": r["solve_s"], "fgmres_iters": r["fgmres_iters"],
+                                   "rel_residual": r["rel_residual"]}
+            if gpu_x is not None:
+                # the GPU solution of the timed steps against the oracle's, everywhere on the grid
+                out["cpu_baseline"]["rel_diff_gpu_vs_oracle"] = float(
+                    np.linalg.norm(gpu_x - r["x"]) / np.linalg.norm(r["x"]))
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -195,6 +195,13 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     const long long len = (long long)s.ext[0] * s.ext[1] * s.ext[2];
     for (long long li = 0; li < len; ++li) {
       int x[3] = {(int)(li % s.ext[0]), (int)((li / s.ext[0]) % s.ext[1]), (int)(li / ((long long)s.ext[0] * s.ext[1]))};
+      // a receiver node lies within ov + 1 nodes inside some face; skip the others at once
+      bool near_face = false;
+      for (int a = 0; a < d; ++a) {
+        const int ql = x[a] - e, qh = e + s.nown[a] - 1 - x[a];
+        near_face = near_face || (ql >= 0 && ql <= ov) || (qh >= 0 && qh <= ov);
+      }
+      if (!near_face) continue;
       unsigned mask = 0;
       for (int code = 0; code < NDIR; ++code) {
         if (code == 13 || s.nbr[code] < 0) continue;
@@ -245,7 +252,7 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
   c->npart = std::max<long long>((long long)R * g.nsub * ((maxlen + 127) / 128 + 1),
                                   (long long)R * 304LL * 2 * 122);
   int* d_tdesc = nullptr;
-#define ALLOC(ptr, bytes) CK(cudaMalloc((void**)&(ptr), (bytes)))
+#define ALLOC(ptr, bytes) CK(dev_alloc(c, (void**)&(ptr), (bytes)))
   ddm_status st = DDM_OK;
   auto body = [&]() -> ddm_status {
     ALLOC(c->d_k2, sizeof(double) * g.nglob);
@@ -261,7 +268,7 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     ALLOC(c->d_err, sizeof(int));
     ALLOC(c->d_part, sizeof(double) * c->npart);
     ALLOC(c->d_scal, sizeof(double) * 64);
-    CK(cudaMallocHost((void**)&c->h_scal, sizeof(double) * 64));
+    CK(host_pinned_alloc((void**)&c->h_scal, sizeof(double) * 64));
     ALLOC(d_tdesc, sizeof(int) * tdesc.size());
     ALLOC(c->d_src, le * g.ltotal * R);
     ALLOC(c->d_U, le * g.ltotal * R);
@@ -269,6 +276,12 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     ALLOC(c->d_gb, sizeof(z64) * g.nglob * R);
     ALLOC(c->d_gr, sizeof(z64) * g.nglob * R);
     ALLOC(c->d_gw, sizeof(z64) * g.nglob * R);
+    ALLOC(c->d_hash, sizeof(unsigned long long) * g.nsub);
+    ALLOC(c->d_pairs, sizeof(int) * 2 * g.nsub);
+    ALLOC(c->d_mis, sizeof(int) * g.nsub);
+    ALLOC(c->d_reps, sizeof(int) * g.nsub);
+    ALLOC(c->d_ldb, sizeof(int) * g.nsub);
+    ALLOC(c->d_fofs, sizeof(long long) * g.nsub);
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
     CK(cudaMemcpyAsync(d_tdesc, tdesc.data(), sizeof(int) * tdesc.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_owner, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice, c->st));
@@ -288,7 +301,7 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     return DDM_OK;
   };
   st = body();
-  if (d_tdesc) cudaFree(d_tdesc);
+  dev_free(c, d_tdesc);
   if (st != DDM_OK) {
     std::string msg = c->err;
     ddm_destroy(c);
@@ -300,21 +313,23 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
 
 extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (!c) return DDM_OK;
-  if (c->st || true) cudaStreamSynchronize(c->st);
+  cudaStreamSynchronize(c->st);
   for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
   if (c->gstream) cudaStreamSynchronize(c->gstream), cudaStreamDestroy(c->gstream);
   for (auto ev : c->gev) if (ev) cudaEventDestroy(ev);
-  if (c->d_gin) cudaFree(c->d_gin);
-  if (c->d_gout) cudaFree(c->d_gout);
-  if (c->h_bscal) cudaFreeHost(c->h_bscal);
-  if (c->d_bscal) cudaFree(c->d_bscal);
-  if (c->d_jr) cudaFree(c->d_jr);
+  dev_free(c, c->d_gin);
+  dev_free(c, c->d_gout);
+  host_pinned_free(c->h_bscal);
+  dev_free(c, c->d_bscal);
+  dev_free(c, c->d_jr);
   void* ptrs[] = {c->d_subs, c->d_k2, c->d_lcoef, c->d_gcoef, c->d_sidx, c->d_smask, c->d_tab, c->d_beta, c->d_owner, c->d_cuts, c->d_err, c->d_part,
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
                   c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs,
-                  c->d_gtc, c->d_ytc, c->d_tcpart, c->d_gtc2, c->d_tc2ofs};
-  for (void* q : ptrs) if (q) cudaFree(q);
-  if (c->h_scal) cudaFreeHost(c->h_scal);
+                  c->d_gtc, c->d_ytc, c->d_tcpart, c->d_gtc2, c->d_tc2ofs, c->d_hash, c->d_pairs, c->d_mis,
+                  c->d_reps, c->d_ldb, c->d_fofs, c->d_coef};
+  for (void* q : ptrs) dev_free(c, q);
+  cudaStreamSynchronize(c->st);   // the frees are stream-ordered: complete them before returning
+  host_pinned_free(c->h_scal);
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   for (auto ev : c->ev_pool) cudaEventDestroy(ev);
   delete c;
@@ -336,7 +351,7 @@ extern "C" ddm_status ddm_set_medium(ddm_ctx* c, double omega, const double* c_d
 extern "C" ddm_status ddm_set_medium_host(ddm_ctx* c, double omega, const double* c_host) {
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
   if (!c_host) return fail(c, DDM_E_INVAL, "c_host is null");
-  if (!c->d_chost) CK(cudaMalloc((void**)&c->d_chost, sizeof(double) * c->g.nglob));
+  if (!c->d_chost) CK(dev_alloc(c, (void**)&c->d_chost, sizeof(double) * c->g.nglob));
   CK(cudaMemcpyAsync(c->d_chost, c_host, sizeof(double) * c->g.nglob, cudaMemcpyHostToDevice, c->st));
   return ddm_set_medium(c, omega, c->d_chost);
 }
@@ -354,13 +369,11 @@ extern "C" ddm_status ddm_kernel_launches(ddm_ctx* c, int64_t* count, int reset)
 extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
   Geom& g = c->g;
-  unsigned long long* d_hash = nullptr;
-  CK(cudaMalloc((void**)&d_hash, sizeof(unsigned long long) * g.nsub));
+  unsigned long long* d_hash = c->d_hash;
   CK(launch_sub_hash(c, d_hash));
   std::vector<unsigned long long> hash(g.nsub);
   CK(cudaMemcpyAsync(hash.data(), d_hash, sizeof(unsigned long long) * g.nsub, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  cudaFree(d_hash);
   // group by (own widths, hash); confirm every member against its group's representative
   std::map<std::tuple<int, int, int, unsigned long long>, int> groups;
   std::vector<int> rep_of(g.nsub);
@@ -374,15 +387,12 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   for (int s = 0; s < g.nsub; ++s) if (rep_of[s] != s) { pairs.push_back(s); pairs.push_back(rep_of[s]); }
   int npairs = (int)pairs.size() / 2;
   if (npairs) {
-    int *d_pairs = nullptr, *d_mis = nullptr;
-    CK(cudaMalloc((void**)&d_pairs, sizeof(int) * pairs.size()));
-    CK(cudaMalloc((void**)&d_mis, sizeof(int) * npairs));
+    int *d_pairs = c->d_pairs, *d_mis = c->d_mis;
     CK(cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, c->st));
     CK(launch_sub_compare(c, d_pairs, npairs, d_mis));
     std::vector<int> mis(npairs);
     CK(cudaMemcpyAsync(mis.data(), d_mis, sizeof(int) * npairs, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    cudaFree(d_pairs); cudaFree(d_mis);
     for (int q = 0; q < npairs; ++q) if (mis[q]) rep_of[pairs[2 * q]] = pairs[2 * q];   // hash collision: own factor
   }
   // factor ids and storage
@@ -410,18 +420,16 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   c->fac_elems = ofs;
   const size_t gbytes = (size_t)ofs * local_elem(c);
   if (gbytes > c->G_cap) {
-    if (c->d_G) { cudaFree(c->d_G); c->d_G = nullptr; }
+    dev_free(c, c->d_G);
+    c->d_G = nullptr;
     c->G_cap = 0;
     c->drop_graphs();
-    CK(cudaMalloc(&c->d_G, gbytes));
+    CK(dev_alloc(c, &c->d_G, gbytes));
     c->G_cap = gbytes;
   }
   CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDesc) * g.nsub, cudaMemcpyHostToDevice, c->st));
-  int *d_reps = nullptr, *d_ldb = nullptr;
-  long long* d_fofs = nullptr;
-  CK(cudaMalloc((void**)&d_reps, sizeof(int) * c->nfac));
-  CK(cudaMalloc((void**)&d_ldb, sizeof(int) * c->nfac));
-  CK(cudaMalloc((void**)&d_fofs, sizeof(long long) * c->nfac));
+  int *d_reps = c->d_reps, *d_ldb = c->d_ldb;
+  long long* d_fofs = c->d_fofs;
   CK(cudaMemcpyAsync(d_reps, reps.data(), sizeof(int) * c->nfac, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(d_ldb, c->fac_ldb.data(), sizeof(int) * c->nfac, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(d_fofs, c->fac_ofs.data(), sizeof(long long) * c->nfac, cudaMemcpyHostToDevice, c->st));
@@ -444,7 +452,6 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
   cudaEventElapsedTime(&c->factor_ms, e0, e1);
   cudaEventDestroy(e0); cudaEventDestroy(e1);
-  cudaFree(d_reps); cudaFree(d_ldb); cudaFree(d_fofs);
   CKS(check_err_word(c));
   c->factored = true;
   return DDM_OK;
@@ -511,8 +518,8 @@ static ddm_status apply_graphed(ddm_ctx* c, const z64* src, z64* dst, int nrhs, 
     CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&c->gev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->gev[1], cudaEventDisableTiming));
-    CK(cudaMalloc((void**)&c->d_gin, sizeof(z64) * n * c->p.max_rhs));
-    CK(cudaMalloc((void**)&c->d_gout, sizeof(z64) * n * c->p.max_rhs));
+    CK(dev_alloc(c, (void**)&c->d_gin, sizeof(z64) * n * c->p.max_rhs));
+    CK(dev_alloc(c, (void**)&c->d_gout, sizeof(z64) * n * c->p.max_rhs));
   }
   ddm_ctx::GraphRec* rec = nullptr;
   for (auto& g : c->graphs) if (g.nrhs == nrhs && g.K == K) rec = &g;
@@ -651,20 +658,21 @@ static double host_norm(ddm_ctx* c, const z64* x, ddm_status* st) {
 
 static ddm_status ensure_krylov(ddm_ctx* c, int m, int nb) {
   if (c->kry_m >= m && c->kry_nb >= nb) return DDM_OK;
-  void* old[] = {c->d_V, c->d_Z, c->d_H, c->d_gs, c->d_bscal, c->d_jr};
-  for (void* q : old) if (q) cudaFree(q);
-  if (c->h_bscal) cudaFreeHost(c->h_bscal);
+  void* old[] = {c->d_V, c->d_Z, c->d_H, c->d_gs, c->d_bscal, c->d_jr, c->d_coef};
+  for (void* q : old) dev_free(c, q);
+  host_pinned_free(c->h_bscal);
   c->d_V = c->d_Z = c->d_H = c->d_gs = nullptr;
-  c->d_bscal = nullptr; c->h_bscal = nullptr; c->d_jr = nullptr;
+  c->d_bscal = nullptr; c->h_bscal = nullptr; c->d_jr = nullptr; c->d_coef = nullptr;
   c->kry_m = c->kry_nb = 0;
   const long long n = c->g.nglob;
-  CK(cudaMalloc((void**)&c->d_V, sizeof(z64) * n * (m + 1) * nb));
-  CK(cudaMalloc((void**)&c->d_Z, sizeof(z64) * n * m * nb));
-  CK(cudaMalloc((void**)&c->d_H, sizeof(z64) * (m + 1) * m * nb));
-  CK(cudaMalloc((void**)&c->d_gs, sizeof(z64) * (5 * m + 4) * nb));
-  CK(cudaMalloc((void**)&c->d_bscal, sizeof(double) * 4 * nb));
-  CK(cudaMallocHost((void**)&c->h_bscal, sizeof(double) * 4 * nb));
-  CK(cudaMalloc((void**)&c->d_jr, sizeof(int) * nb));
+  CK(dev_alloc(c, (void**)&c->d_V, sizeof(z64) * n * (m + 1) * nb));
+  CK(dev_alloc(c, (void**)&c->d_Z, sizeof(z64) * n * m * nb));
+  CK(dev_alloc(c, (void**)&c->d_H, sizeof(z64) * (m + 1) * m * nb));
+  CK(dev_alloc(c, (void**)&c->d_gs, sizeof(z64) * (5 * m + 4) * nb));
+  CK(dev_alloc(c, (void**)&c->d_bscal, sizeof(double) * 4 * nb));
+  CK(host_pinned_alloc((void**)&c->h_bscal, sizeof(double) * 4 * nb));
+  CK(dev_alloc(c, (void**)&c->d_jr, sizeof(int) * nb));
+  CK(dev_alloc(c, (void**)&c->d_coef, sizeof(z64) * (m + 1) * nb));
   c->kry_m = m;
   c->kry_nb = nb;
   return DDM_OK;
@@ -689,9 +697,8 @@ static ddm_status fgmres_batch(ddm_ctx* c, const z64* b, z64* x, int nb, double 
   z64* gs = c->d_gs;
   const int GSZ = 5 * m + 4;
   // coefficient scratch for the Gram-Schmidt passes: nb x (m+1), after the gs blocks' y part
-  z64* coef = nullptr;
-  CK(cudaMalloc((void**)&coef, sizeof(z64) * (m + 1) * nb));
-  auto cleanup = [&]() { cudaFree(coef); };
+  z64* coef = c->d_coef;
+  auto cleanup = [&]() {};
   auto batch_norms = [&](const z64* v) -> ddm_status {
     int nblk = 0;
     CK(launch_norm2_partial(c, v, n, nb, c->d_part, &nblk));
@@ -885,7 +892,7 @@ extern "C" ddm_status ddm_solve_host(ddm_ctx* c, const void* f_host, void* u_hos
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
   if (nrhs < 1 || nrhs > c->p.max_rhs || !f_host || !u_host) return fail(c, DDM_E_INVAL, "bad nrhs / pointer");
   const long long n = c->g.nglob;
-  if (!c->d_hostbuf) CK(cudaMalloc((void**)&c->d_hostbuf, sizeof(z64) * n * c->p.max_rhs * 2));
+  if (!c->d_hostbuf) CK(dev_alloc(c, (void**)&c->d_hostbuf, sizeof(z64) * n * c->p.max_rhs * 2));
   z64* f = c->d_hostbuf;
   z64* u = c->d_hostbuf + n * c->p.max_rhs;
   CK(cudaMemcpyAsync(f, f_host, sizeof(z64) * n * nrhs, cudaMemcpyHostToDevice, c->st));
@@ -1052,5 +1059,69 @@ cudaError_t allow_dynamic_smem(const void* func, size_t need) {
     return e;
   done.insert({func, dev});
   return cudaSuccess;
+}
+}  // namespace ddm
+
+// ------------------------------------------------------------------------------------------
+// device and pinned host memory of the contexts
+namespace ddm {
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;          // device ordinal -> the library's pool
+std::mutex g_pin_mu;
+std::multimap<size_t, void*> g_pin_free;       // released pinned blocks by size
+std::map<void*, size_t> g_pin_size;            // every pinned block handed out, by address
+
+cudaError_t pool_of_current_device(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) { *out = it->second; return cudaSuccess; }
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+  g_pools[dev] = pool;
+  *out = pool;
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t dev_alloc(ddm_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = pool_of_current_device(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, c->st);
+}
+
+void dev_free(ddm_ctx* c, void* p) {
+  if (p) cudaFreeAsync(p, c->st);
+}
+
+cudaError_t host_pinned_alloc(void** p, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  auto it = g_pin_free.lower_bound(bytes);
+  if (it != g_pin_free.end() && it->first <= 2 * bytes + 4096) {
+    *p = it->second;
+    g_pin_free.erase(it);
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMallocHost(p, bytes);
+  if (e == cudaSuccess) g_pin_size[*p] = bytes;
+  return e;
+}
+
+void host_pinned_free(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  auto it = g_pin_size.find(p);
+  if (it != g_pin_size.end()) g_pin_free.insert({it->second, p});
 }
 }  // namespace ddm

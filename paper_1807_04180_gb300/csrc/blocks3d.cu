@@ -407,17 +407,19 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   int bmax = 0;
   for (size_t f = 0; f < reps.size(); ++f) bmax = std::max(bmax, c->fac_b[f]);
   const int ldw = bmax;
-  // scratch buffers, freed when the function returns (allocation failures return before any
-  // launch; the normal path synchronises the stream first)
+  // scratch buffers, released on every return path by stream-ordered frees on the context's
+  // stream (after the launches that use them)
   struct Scratch {
+    ddm_ctx* c;
     void* p[8] = {};
     int n = 0;
+    explicit Scratch(ddm_ctx* cc) : c(cc) {}
     ~Scratch() {
-      for (int i = 0; i < n; ++i) cudaFree(p[i]);
+      for (int i = 0; i < n; ++i) dev_free(c, p[i]);
     }
-  } scratch;
+  } scratch(c);
   auto alloc = [&](void** ptr, size_t bytes) {
-    const cudaError_t r = cudaMalloc(ptr, bytes);
+    const cudaError_t r = dev_alloc(c, ptr, bytes);
     if (r == cudaSuccess) scratch.p[scratch.n++] = *ptr;
     return r;
   };
@@ -573,9 +575,9 @@ static cudaError_t solve3d_t(ddm_ctx* c, const void* src, void* out, void* U, in
     const int ncol = (int)cols[f].size();
     if (!ncol) continue;
     if ((size_t)ncol > c->col3d_cap) {
-      if (c->d_col3d) cudaFree(c->d_col3d);
+      dev_free(c, c->d_col3d);
       c->d_col3d = nullptr;
-      if ((e = cudaMalloc((void**)&c->d_col3d, sizeof(long long) * ncol)) != cudaSuccess) return e;
+      if ((e = dev_alloc(c, (void**)&c->d_col3d, sizeof(long long) * ncol)) != cudaSuccess) return e;
       c->col3d_cap = ncol;
     }
     if ((e = cudaMemcpyAsync(c->d_col3d, cols[f].data(), sizeof(long long) * ncol, cudaMemcpyHostToDevice, c->st)) !=

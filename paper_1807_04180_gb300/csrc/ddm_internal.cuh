@@ -247,10 +247,28 @@ struct ddm_ctx {
   long long t_n[ddm::T_NSLOT] = {0};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  // per-call scratch of ddm_factor and of FGMRES, sized once (no allocation per call)
+  unsigned long long* d_hash = nullptr;   // nsub
+  int* d_pairs = nullptr;                 // 2 nsub
+  int* d_mis = nullptr;                   // nsub
+  int* d_reps = nullptr;                  // nsub
+  int* d_ldb = nullptr;                   // nsub
+  long long* d_fofs = nullptr;            // nsub
+  ddm::z64* d_coef = nullptr;             // (kry_m + 1) x kry_nb Gram-Schmidt coefficients
   std::string err;
 };
 
 namespace ddm {
+// Device memory of a context: stream-ordered allocations (cudaMallocFromPoolAsync on the
+// context's stream) from one memory pool of the library per device, so that creating and
+// destroying contexts neither synchronises the device nor stalls work of other contexts (as
+// cudaMalloc / cudaFree can).  Freed memory returns to the pool.  dev_free(nullptr) is a no-op.
+cudaError_t dev_alloc(ddm_ctx* c, void** p, size_t bytes);
+void dev_free(ddm_ctx* c, void* p);
+// Pinned host buffers from a process-wide free list (cudaFreeHost can synchronise the device).
+cudaError_t host_pinned_alloc(void** p, size_t bytes);
+void host_pinned_free(void* p);
+
 // launchers implemented in the .cu files (all enqueue on ctx->st)
 cudaError_t launch_build_tables(ddm_ctx* c, const int* d_tdesc, int ntab, double sigma0, double power, int npml);
 cudaError_t launch_k2(ddm_ctx* c, const double* c_dev);

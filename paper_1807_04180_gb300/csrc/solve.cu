@@ -330,7 +330,7 @@ static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int 
     // scratch output and accumulator: the candidates are timed with the accumulation the DDM
     // steps ask for
     void* scratch = nullptr;
-    cudaError_t e = cudaMalloc(&scratch, 2 * sizeof(cplx<T>) * c->g.ltotal * nrhs);
+    cudaError_t e = dev_alloc(c, &scratch, 2 * sizeof(cplx<T>) * c->g.ltotal * nrhs);
     if (e != cudaSuccess) return e;
     void* uscratch = (char*)scratch + sizeof(cplx<T>) * c->g.ltotal * nrhs;
     cudaMemsetAsync(uscratch, 0, sizeof(cplx<T>) * c->g.ltotal * nrhs, c->st);
@@ -355,7 +355,7 @@ static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(scratch);
+    dev_free(c, scratch);
     if (e != cudaSuccess) return e;
     // a context that tuned the same shapes at the same time may have been first: use its choice
     std::lock_guard<std::mutex> lk(g_tune_mu);

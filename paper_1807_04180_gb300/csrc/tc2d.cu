@@ -485,23 +485,23 @@ cudaError_t tc2d_pack_factors(ddm_ctx* c) {
   }
   // grow-only: a captured graph of M_K keeps addressing these buffers
   if ((size_t)total > c->gtc2_cap) {
-    if (c->d_gtc2) cudaFree(c->d_gtc2);
+    dev_free(c, c->d_gtc2);
     c->d_gtc2 = nullptr;
     c->gtc2_cap = 0;
     c->drop_graphs();
-    if ((e = cudaMalloc((void**)&c->d_gtc2, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
+    if ((e = dev_alloc(c, (void**)&c->d_gtc2, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
     c->gtc2_cap = (size_t)total;
   }
   if ((size_t)c->nfac > c->tc2ofs_cap) {
-    if (c->d_tc2ofs) cudaFree(c->d_tc2ofs);
+    dev_free(c, c->d_tc2ofs);
     c->d_tc2ofs = nullptr;
     c->tc2ofs_cap = 0;
     c->drop_graphs();
-    if ((e = cudaMalloc((void**)&c->d_tc2ofs, sizeof(long long) * c->nfac)) != cudaSuccess) return e;
+    if ((e = dev_alloc(c, (void**)&c->d_tc2ofs, sizeof(long long) * c->nfac)) != cudaSuccess) return e;
     c->tc2ofs_cap = (size_t)c->nfac;
   }
   TC2Fac* d_facs = nullptr;
-  if ((e = cudaMalloc((void**)&d_facs, sizeof(TC2Fac) * c->nfac)) != cudaSuccess) return e;
+  if ((e = dev_alloc(c, (void**)&d_facs, sizeof(TC2Fac) * c->nfac)) != cudaSuccess) return e;
   cudaMemcpyAsync(d_facs, facs.data(), sizeof(TC2Fac) * c->nfac, cudaMemcpyHostToDevice, c->st);
   cudaMemcpyAsync(c->d_tc2ofs, c->tc2_ofs.data(), sizeof(long long) * c->nfac, cudaMemcpyHostToDevice, c->st);
   const int gx = (int)std::min<long long>(64, (maxel / 4 + 255) / 256 + 1);
@@ -509,7 +509,7 @@ cudaError_t tc2d_pack_factors(ddm_ctx* c) {
   k_g2_pack<<<dim3(gx, c->nfac), 256, 0, c->st>>>(d_facs, (const c32*)c->d_G, c->d_gtc2);
   e = cudaGetLastError();
   cudaStreamSynchronize(c->st);
-  cudaFree(d_facs);
+  dev_free(c, d_facs);
   return e;
 }
 

@@ -282,10 +282,10 @@ cudaError_t tc3d_pack_factors(ddm_ctx* c) {
     total += tc3d_packed_floats(c->fac_b[f], c->fac_m[f]);
   }
   if ((size_t)total > c->gtc_cap) {
-    if (c->d_gtc) cudaFree(c->d_gtc);
+    dev_free(c, c->d_gtc);
     c->d_gtc = nullptr;
     c->gtc_cap = 0;
-    if ((e = cudaMalloc((void**)&c->d_gtc, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
+    if ((e = dev_alloc(c, (void**)&c->d_gtc, sizeof(float) * (size_t)total)) != cudaSuccess) return e;
     c->gtc_cap = (size_t)total;
   }
   for (int f = 0; f < c->nfac; ++f) {
@@ -308,10 +308,10 @@ cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, 
   const int nQT = (ncol + TC3_TILE - 1) / TC3_TILE;
   const size_t need = (size_t)nQT * nKC * TC3_BLOCK;   // one operand buffer; two are kept
   if (need > c->ytc_cap) {
-    if (c->d_ytc) cudaFree(c->d_ytc);
+    dev_free(c, c->d_ytc);
     c->d_ytc = nullptr;
     c->ytc_cap = 0;
-    if ((e = cudaMalloc((void**)&c->d_ytc, sizeof(float) * 2 * need)) != cudaSuccess) return e;
+    if ((e = dev_alloc(c, (void**)&c->d_ytc, sizeof(float) * 2 * need)) != cudaSuccess) return e;
     // padding rows (columns q >= ncol) stay zero in both buffers
     if ((e = cudaMemsetAsync(c->d_ytc, 0, sizeof(float) * 2 * need, c->st)) != cudaSuccess) return e;
     c->ytc_cap = need;
@@ -324,10 +324,10 @@ cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, 
   const int nsplit = std::max(1, std::min({8, nKC, std::max(nsm, 1) / tiles}));
   const size_t pneed = (size_t)tiles * nsplit * TC3_TILE * 2 * TC3_TILE;
   if (pneed > c->tcpart_cap) {
-    if (c->d_tcpart) cudaFree(c->d_tcpart);
+    dev_free(c, c->d_tcpart);
     c->d_tcpart = nullptr;
     c->tcpart_cap = 0;
-    if ((e = cudaMalloc((void**)&c->d_tcpart, sizeof(float) * pneed)) != cudaSuccess) return e;
+    if ((e = dev_alloc(c, (void**)&c->d_tcpart, sizeof(float) * pneed)) != cudaSuccess) return e;
     c->tcpart_cap = pneed;
   }
   const long long etotal = (long long)tiles * TC3_TILE * TC3_TILE;

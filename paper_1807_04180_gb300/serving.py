@@ -1,9 +1,14 @@
 """Serving loop for DDM Helmholtz solves on one GPU: continuous batching with HBM-budget admission.
 
 Requests (a workloads.Workload: grid, partition, medium c, sources f with 1..R right-hand
-sides) are queued on submit().  A scheduler thread admits queued requests in arrival order,
-first fit, whenever the free slots and the HBM budget allow: a request's device footprint is
-the library's own upper bound (ddm_workspace_bytes) plus its input/output buffers.  Each
+sides) are queued on submit().  A scheduler thread admits queued requests whenever the free
+slots and the HBM budget allow: a request's device footprint is the library's own upper bound
+(ddm_workspace_bytes) plus its input/output buffers.  Among the queued requests that fit, the
+default policy ("hrrn", highest response ratio next) admits the one with the largest
+(waiting time + expected service) / expected service, the expected service being the request's
+work (grid nodes x right-hand sides) times the seconds per unit of work measured on the
+requests completed so far: short requests pass long ones, and a long request's ratio grows
+while it waits, so none starves.  Policy "fifo" admits the first that fits in arrival order.  Each
 admitted request runs on its own CUDA stream and library context -- set-up, factorisation and
 the batched FGMRES solve stay resident on the device until it finishes -- so requests that
 arrive while others are running join them and their kernels overlap on the device.  Every
@@ -50,7 +55,8 @@ class DDMServer:
 
     def __init__(self, device: int = 0, hbm_budget: Optional[int] = None, budget_fraction: float = 0.8,
                  max_active: int = 8, precision: int = D.DDM_MIXED, K: int = 16, restart: int = 20,
-                 max_it: int = 400, keep_results: bool = True):
+                 max_it: int = 400, keep_results: bool = True, policy: str = "hrrn",
+                 collect_timing: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -61,6 +67,13 @@ class DDMServer:
         self.precision = precision
         self.K, self.restart, self.max_it = K, restart, max_it
         self.keep_results = keep_results
+        if policy not in ("hrrn", "fifo"):
+            raise ValueError("policy must be 'hrrn' or 'fifo'")
+        self.policy = policy
+        # collect_timing: record each request's kernel times (the library's per-launch CUDA
+        # events) and the algorithmic bytes of its local solves in its info dict
+        self.collect_timing = collect_timing
+        self._rate = 3e-8           # seconds per grid node and right-hand side, updated online
         self._cv = threading.Condition()
         self._queue: List[Request] = []
         self._reqs: Dict[int, Request] = {}
@@ -149,15 +162,33 @@ class DDMServer:
                 "peak_active": self._peak_active, "budget_bytes": self.budget}
 
     # ------------------------------------------------------------------ internals
+    @staticmethod
+    def work(wl) -> float:
+        """A request's work in grid nodes x right-hand sides (its service time is about
+        proportional to it at a fixed number of points per wavelength)."""
+        return float(np.prod(wl.c.shape)) * max(1, int(wl.nrhs))
+
+    def _pick(self, now: float) -> Optional[Request]:
+        """The queued request to admit now (caller holds the lock), or None."""
+        fits = [r for r in self._queue if self._used + r.nbytes <= self.budget]
+        if not fits:
+            return None
+        if self.policy == "fifo":
+            return fits[0]                   # first fit, in arrival order
+        best, best_ratio = None, -1.0
+        for r in fits:                       # highest response ratio; ties to the earliest
+            est = max(self.work(r.wl) * self._rate, 1e-6)
+            ratio = (now - r.t_submit + est) / est
+            if ratio > best_ratio:
+                best, best_ratio = r, ratio
+        return best
+
     def _scheduler(self):
         with self._cv:
             while not self._stop:
                 admitted = None
                 if self._active < self.max_active:
-                    for req in self._queue:          # first fit, in arrival order
-                        if self._used + req.nbytes <= self.budget:
-                            admitted = req
-                            break
+                    admitted = self._pick(time.perf_counter())
                 if admitted is None:
                     self._cv.wait(0.05)
                     continue
@@ -185,9 +216,17 @@ class DDMServer:
                 u_dev = torch.zeros(wl.f.shape, dtype=torch.complex128, device=self.device)
                 params, keep = D.params_from(wl, self.precision, max_rhs=wl.nrhs)
                 ctx = D.ddm_setup(params, wl.omega, c_dev, stream)
+                if self.collect_timing:
+                    D.ddm_timing(ctx, enable=True, reset=True)
                 D.ddm_factor(ctx)
                 info = D.ddm_solve(ctx, f_dev, u_dev, nrhs=wl.nrhs, tol=req.tol, max_it=self.max_it,
                                    mode=D.DDM_FGMRES, K=req.K, restart=req.restart, check=True)
+                if self.collect_timing:
+                    info["kernel_ms"] = D.ddm_timing(ctx, enable=False)
+                    per_solve, _ = D.ddm_factor_bytes(ctx)
+                    el = 8 if self.precision == D.DDM_MIXED else 16
+                    # factor once per sweep pair, source read, t written and read, x written
+                    info["local_solve_bytes"] = per_solve + 4 * el * D.ddm_local_layout(ctx)["total"] * wl.nrhs
                 if self.keep_results:
                     result = u_dev.cpu().numpy()
                 stream.synchronize()
@@ -201,6 +240,9 @@ class DDMServer:
                 req.result, req.info, req.error = result, info, error
                 req.t_done = time.perf_counter()
                 req.status = status
+                if status == "done":         # seconds per unit of work, smoothed
+                    obs = (req.t_done - req.t_admit) / max(self.work(req.wl), 1.0)
+                    self._rate = 0.7 * self._rate + 0.3 * obs
                 self._used -= req.nbytes
                 self._active -= 1
                 self._cv.notify_all()

@@ -25,16 +25,19 @@ def test_denominators_are_the_measured_peaks(bench):
         pytest.skip("no measured peaks in this checkout")
     d = json.load(open(path))
     assert bench.peaks() == {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
-    v, src = bench.tf32_peak()
-    assert v == pytest.approx(d["bf16_tflops_sustained"] * 1.1 / 2.25, rel=1e-12)   # nominal TF32 / BF16
-    assert "sustained" in src
+    v, src, recipe = bench.tf32_peak()
+    # the measured per-SM kind::tf32 rate (4096 flop/cycle/SM) x 152 SMs x the maximum clock
+    assert v == pytest.approx(4096 * 152 * d["sm_max_mhz"] * 1e6 / 1e12, rel=1e-12)
+    assert recipe == pytest.approx(d["bf16_tflops_sustained"] * 1.1 / 2.25, rel=1e-12)   # nominal TF32 / BF16
+    v2, src2, _ = bench.tf32_peak(1500.0)                  # the clock sampled during the run
+    assert v2 == pytest.approx(4096 * 152 * 1500e6 / 1e12) and "1500 MHz" in src2
 
 
 def test_denominators_fall_back_without_the_file(bench, monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.peaks() == {"hbm_gbs": 6800.0, "src": "fallback"}
-    v, src = bench.tf32_peak()
-    assert v == pytest.approx(1700.0 * 1.1 / 2.25) and src.startswith("fallback")
+    v, src, recipe = bench.tf32_peak()
+    assert v == pytest.approx(4096 * 152 * 2070e6 / 1e12) and recipe == pytest.approx(1700.0 * 1.1 / 2.25)
 
 
 def test_traffic_only_for_the_captured_source(bench, monkeypatch, tmp_path):

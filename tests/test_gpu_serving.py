@@ -36,6 +36,11 @@ def test_results_same_alone_and_in_the_mix():
         assert got.info["converged"] and got.info["rel_residual"] <= 1e-8
         assert np.linalg.norm(got.result - r) <= 1e-12 * np.linalg.norm(r)
     assert st["p99_ms"] >= st["p50_ms"] > 0
+    # the mix really ran together: several requests were admitted at once and their
+    # admission-to-completion intervals overlap in time
+    assert st["peak_active"] > 1, st
+    spans = sorted((mix.poll(i).t_admit, mix.poll(i).t_done) for i in ids)
+    assert any(spans[k + 1][0] < spans[k][1] for k in range(len(spans) - 1)), spans
 
 
 def test_budget_admission_serialises_and_rejects():

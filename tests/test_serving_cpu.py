@@ -19,13 +19,13 @@ from paper_1807_04180_gb300 import serving as S
 
 
 class FakeWorkload:
-    def __init__(self, nbytes, nrhs=1, fail=False):
+    def __init__(self, nbytes, nrhs=1, fail=False, n=4):
         self.nbytes = nbytes
         self.nrhs = nrhs
         self.fail = fail
         self.omega = 1.0
-        self.c = np.zeros((4, 4))
-        self.f = np.zeros((nrhs, 4, 4), dtype=complex)
+        self.c = np.zeros((n, n))
+        self.f = np.zeros((nrhs, n, n), dtype=complex)
 
 
 def fake_torch():
@@ -53,7 +53,7 @@ class Harness:
     """A DDMServer with host fakes for the device: each request's factorisation blocks on a
     per-request event; `running` records the admitted workloads in admission order."""
 
-    def __init__(self, monkeypatch, budget, max_active):
+    def __init__(self, monkeypatch, budget, max_active, policy="fifo"):
         self.release = {}
         self.running = []
         self.lock = threading.Lock()
@@ -66,6 +66,8 @@ class Harness:
         srv.precision = D.DDM_MIXED
         srv.K, srv.restart, srv.max_it = 16, 20, 10
         srv.keep_results = True
+        srv.policy = policy
+        srv._rate = 3e-8
         srv._cv = threading.Condition()
         srv._queue = []
         srv._reqs = {}
@@ -173,4 +175,60 @@ def test_cancel_queued_and_refuse_oversized(monkeypatch):
     time.sleep(0.05)
     assert h.running == [first]                # the cancelled request never ran
     assert h.srv._used == 0
+    h.srv.shutdown()
+
+
+def _policy_server(policy, rate=1e-6, budget=100):
+    srv = object.__new__(S.DDMServer)
+    srv.policy, srv._rate, srv.budget, srv._used, srv._queue = policy, rate, budget, 0, []
+    return srv
+
+
+def _queued(srv, wl, waited_s, now):
+    r = S.Request(len(srv._queue) + 1, wl, 1e-6, 16, 20, wl.nbytes)
+    r.t_submit = now - waited_s
+    srv._queue.append(r)
+    return r
+
+
+def test_hrrn_admits_short_requests_first_and_ages_long_ones():
+    now = 1000.0
+    # work = nodes x rhs: big 400^2 x 16 = 2.56e6 (est 2.56 s at 1e-6 s per unit), small 16 (est 16 us)
+    srv = _policy_server("hrrn")
+    big = _queued(srv, FakeWorkload(10, nrhs=16, n=400), waited_s=1.0, now=now)
+    small = _queued(srv, FakeWorkload(10, n=4), waited_s=0.5, now=now)
+    assert srv._pick(now) is small              # arrived later, but its ratio is far higher
+    fifo = _policy_server("fifo")
+    fifo._queue = list(srv._queue)
+    assert fifo._pick(now) is big               # arrival order
+    # aging: once the long request has waited many times its expected service, it goes first
+    srv2 = _policy_server("hrrn")
+    old = _queued(srv2, FakeWorkload(10, nrhs=16, n=400), waited_s=60.0, now=now)   # ratio ~24
+    new = _queued(srv2, FakeWorkload(10, nrhs=1, n=100), waited_s=0.0, now=now)      # ratio 1
+    assert srv2._pick(now) is old
+    # the budget still applies: a request that does not fit is skipped
+    srv3 = _policy_server("hrrn", budget=50)
+    _queued(srv3, FakeWorkload(60, n=4), waited_s=5.0, now=now)
+    fit = _queued(srv3, FakeWorkload(40, n=400), waited_s=0.0, now=now)
+    assert srv3._pick(now) is fit
+    srv3._queue = srv3._queue[:1]
+    assert srv3._pick(now) is None
+
+
+def test_hrrn_server_runs_every_request_and_learns_its_rate(monkeypatch):
+    h = Harness(monkeypatch, budget=100, max_active=1, policy="hrrn")
+    first = FakeWorkload(10, n=4)
+    big, small = FakeWorkload(10, nrhs=16, n=400), FakeWorkload(10, n=4)
+    i1 = h.submit(first)
+    assert h.wait_running(1)
+    ib, i_s = h.submit(big), h.submit(small)
+    rate0 = h.srv._rate
+    h.release[id(first)].set()
+    assert h.wait_running(2)
+    assert h.running[1] is small                # the short request passes the long one
+    h.release[id(small)].set()
+    h.release[id(big)].set()
+    assert h.srv.wait(timeout=5.0)
+    assert [h.srv.poll(i).status for i in (i1, ib, i_s)] == ["done"] * 3
+    assert h.srv._rate != rate0                 # updated from the completed requests
     h.srv.shutdown()

@@ -282,6 +282,7 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     ALLOC(c->d_reps, sizeof(int) * g.nsub);
     ALLOC(c->d_ldb, sizeof(int) * g.nsub);
     ALLOC(c->d_fofs, sizeof(long long) * g.nsub);
+    ALLOC(c->d_fsel, sizeof(int) * g.nsub);
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
     CK(cudaMemcpyAsync(d_tdesc, tdesc.data(), sizeof(int) * tdesc.size(), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(c->d_owner, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice, c->st));
@@ -326,7 +327,7 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
                   c->d_scal, c->d_G, c->d_src, c->d_U, c->d_ring[0], c->d_ring[1], c->d_ring[2], c->d_gb,
                   c->d_gr, c->d_gw, c->d_hostbuf, c->d_chost, c->d_col3d, c->d_V, c->d_Z, c->d_H, c->d_gs,
                   c->d_gtc, c->d_ytc, c->d_tcpart, c->d_gtc2, c->d_tc2ofs, c->d_hash, c->d_pairs, c->d_mis,
-                  c->d_reps, c->d_ldb, c->d_fofs, c->d_coef};
+                  c->d_reps, c->d_ldb, c->d_fofs, c->d_fsel, c->d_coef};
   for (void* q : ptrs) dev_free(c, q);
   cudaStreamSynchronize(c->st);   // the frees are stream-ordered: complete them before returning
   host_pinned_free(c->h_scal);

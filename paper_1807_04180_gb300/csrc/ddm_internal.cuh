@@ -254,6 +254,7 @@ struct ddm_ctx {
   int* d_reps = nullptr;                  // nsub
   int* d_ldb = nullptr;                   // nsub
   long long* d_fofs = nullptr;            // nsub
+  int* d_fsel = nullptr;                  // nsub: factor ids in launch order (by kernel variant)
   ddm::z64* d_coef = nullptr;             // (kry_m + 1) x kry_nb Gram-Schmidt coefficients
   std::string err;
 };

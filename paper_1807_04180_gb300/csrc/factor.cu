@@ -267,29 +267,284 @@ __global__ void __launch_bounds__(FAC_THREADS, sizeof(T) == 4 ? 2 : 1) k_factor2
   if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
 }
 
+// ---------------------------------------------------------------------------------------------
+// complex64 factorisation with the Schur block held in registers.
+//
+// Same recurrence and output as k_factor2d.  Each D_k is inverted by Gauss-Jordan with partial
+// (row) pivoting, the pivots applied implicitly: the pivot of step c is the unpivoted row r_c of
+// largest |D[r][c]|, rows are never moved, and after the last step the stored matrix M satisfies
+// D^{-1}[i][l] = M[r_i][c(l)] with c(l) the step whose pivot row is l.  Layout: warp w holds
+// columns [8w, 8w + 8) of all rows in registers, lane l the rows l + 32 t, t < RL.  The columns are
+// eliminated in panels of 8 (one warp's strip).  The owner of panel P eliminates it alone, in its
+// registers: pivot search by warp shuffles on a key that packs |D|^2 (low mantissa bits dropped)
+// with the row, the pivot row broadcast by shuffles.  It then publishes the panel's new columns X
+// (the block Gauss-Jordan multipliers) and pivot rows.  Every other warp applies the step to its
+// own columns as one rank-8 update,
+//     M[i][j] = [i not a pivot row of P] M[i][j] + sum_q X[i][q] T[q][j],
+// T[q][j] being the old value of pivot row r_q in column j.  T comes from the warp's own strip,
+// mirrored in shared memory once per panel.  Look-ahead: the owner of panel P + 1 applies panel
+// P's update to its strip and eliminates panel P + 1 while the other warps apply panel P, so each
+// panel costs one CTA barrier.  At the end of a line the strips go to shared memory.  The
+// permuted inverse is then written to global memory (column-major, as k_factor2d) and read back
+// for the next line's Schur complement.
+template <int RL>
+struct FacRG {
+  static constexpr int ROWS = 32 * RL;        // rows held (b <= ROWS)
+  static constexpr int LDC = ROWS + 2;        // row stride of the shared mirror (== 2 mod 16)
+  static constexpr int NWARP = ROWS / 8;      // column strips of 8
+  static constexpr int THREADS = 32 * NWARP;
+  static size_t smem() {
+    return sizeof(c32) * ((size_t)ROWS * LDC + 2 * 8 * ROWS + 6 * ROWS) + 2 * sizeof(int) * ROWS;
+  }
+};
+
+// Eliminate the 8 columns of panel pe held in R (rows lane + 32 t) with the rows flagged in pm
+// excluded from the pivot search; writes the panel's new columns to X (column-major, ROWS per
+// column) and its pivot rows to piv[8 pe + q].
+template <int RL>
+__device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][8], unsigned pm, const int pe, const int b, const int lane,
+                                             c32* X, int* piv, int* s_bad) {
+  constexpr int ROWS = FacRG<RL>::ROWS;
+  const int w = min(8, b - 8 * pe);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q >= w) break;
+    // pivot: the unpivoted row of largest |M[r][c]|^2 (ties to the lowest row)
+    unsigned key = 0u;
+#pragma unroll
+    for (int t = 0; t < RL; ++t) {
+      const int i = lane + 32 * t;
+      if (i < b && !((pm >> t) & 1u)) {
+        const unsigned kk = (__float_as_uint(cabs2(R[t][q])) & 0xFFFFFF00u) | (unsigned)(255 - i);
+        key = max(key, kk);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+    const int r = key ? 255 - (int)(key & 0xFFu) : 0;
+    const int tr = r >> 5, lr = r & 31;
+    // the pivot row's 8 values, from lane lr
+    c32 sv[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      c32 v = R[0][jj];
+#pragma unroll
+      for (int t = 1; t < RL; ++t)
+        if (tr == t) v = R[t][jj];
+      sv[jj].x = __shfl_sync(0xffffffffu, v.x, lr);
+      sv[jj].y = __shfl_sync(0xffffffffu, v.y, lr);
+    }
+    const float pa = cabs2(sv[q]);
+    const bool ok = key != 0u && pa > 0.f && isfinite(pa);
+    if (!ok && lane == 0) *s_bad = 1;
+    const c32 inv = ok ? cinv(sv[q]) : mk<float>(0.f, 0.f);
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) sv[jj] = jj == q ? inv : sv[jj] * inv;
+    // row r becomes the scaled pivot row; every other row i loses f_i = M[i][c] times it, and
+    // its column c becomes -f_i / p
+#pragma unroll
+    for (int t = 0; t < RL; ++t) {
+      const bool isr = lane + 32 * t == r;
+      const c32 f = isr ? mk<float>(-1.f, 0.f) : R[t][q];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        c32 base = (isr || jj == q) ? mk<float>(0.f, 0.f) : R[t][jj];
+        cfma(base, -f, sv[jj]);
+        R[t][jj] = base;
+      }
+    }
+    if (lane == lr) pm |= 1u << tr;
+    if (lane == 0) piv[8 * pe + q] = r;
+  }
+#pragma unroll
+  for (int t = 0; t < RL; ++t)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) X[q * ROWS + lane + 32 * t] = R[t][q];
+}
+
+template <int RL>
+__global__ void __launch_bounds__(FacRG<RL>::THREADS, RL == 3 ? 2 : 1)
+    k_factor2d_rg(Geom g, const int* fsel, int fsel_ofs, const int* reps, const long long* fofs_arr, const int* ldbs,
+                  c32* Gout, int* err) {
+  constexpr int ROWS = FacRG<RL>::ROWS, LDC = FacRG<RL>::LDC;
+  extern __shared__ __align__(16) unsigned char smem[];
+  c32* Mst = (c32*)smem;                 // ROWS x LDC mirror of the strips (row-major)
+  c32* Xb = Mst + ROWS * LDC;            // 2 x (8 columns x ROWS): published panel columns
+  c32* cC = Xb + 2 * 8 * ROWS;           // centre of line k
+  c32* cE = cC + ROWS;                   // x+ coupling
+  c32* cW = cE + ROWS;                   // x- coupling
+  c32* cS = cW + ROWS;                   // coupling of line k to line k-1
+  c32* cNn = cS + ROWS;                  // coupling of line k to line k+1
+  c32* cNp = cNn + ROWS;                 // coupling of line k-1 to line k
+  int* piv = (int*)(cNp + ROWS);         // pivot row of each elimination step
+  int* rinv = piv + ROWS;                // step whose pivot row is l
+  __shared__ int s_bad;
+  const int f = fsel[fsel_ofs + blockIdx.x];
+  const SubDesc& sd = g.subs[reps[f]];
+  const long long fofs = fofs_arr[f];
+  const int ldb = ldbs[f];
+  const int b = sd.ext[0], m = sd.ext[1];
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int npan = (b + 7) >> 3;
+  const int col0 = 8 * warp;
+  const bool has_cols = col0 < b;
+  if (tid == 0) s_bad = 0;
+  c32 R[RL][8];
+  for (int k = 0; k <= m; ++k) {
+    if (k < m) {
+      const long long len = (long long)b * m;
+      const c32* lc = (const c32*)g.lcoef + sd.vofs * 5 + (long long)k * b;
+      for (int i = tid; i < ROWS; i += nth) {
+        const bool v = i < b;
+        const c32 z = mk<float>(0.f, 0.f);
+        cC[i] = v ? lc[i] : z;
+        cW[i] = v ? lc[len + i] : z;
+        cE[i] = v ? lc[2 * len + i] : z;
+        cS[i] = v ? lc[3 * len + i] : z;
+        cNn[i] = v ? lc[4 * len + i] : z;
+      }
+    }
+    __syncthreads();   // line k's couplings; line k-1's final strips, pivots and rinv
+    if (k > 0) {       // G_(k-1)[i][j] = M[r_i][rinv[j]], column j contiguous
+      c32* Gk = Gout + fofs + (long long)(k - 1) * b * ldb;
+      for (int idx = tid; idx < b * ldb; idx += nth) {
+        const int j = idx / ldb, i = idx - j * ldb;
+        Gk[idx] = i < b ? Mst[piv[i] * LDC + rinv[j]] : mk<float>(0.f, 0.f);
+      }
+    }
+    if (k == m) break;
+    // D_k = T_k - L_k G_(k-1) U_(k-1) into the registers of this warp's strip
+#pragma unroll
+    for (int t = 0; t < RL; ++t) {
+      const int i = lane + 32 * t;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = col0 + jj;
+        c32 d = mk<float>(0.f, 0.f);
+        if (i < b && j < b) {
+          if (k > 0) d = -(cS[i] * Mst[piv[i] * LDC + rinv[j]] * cNp[j]);
+          if (j == i) d = d + cC[i];
+          if (j == i + 1) d = d + cE[i];
+          if (j == i - 1) d = d + cW[i];
+        }
+        R[t][jj] = d;
+      }
+    }
+    unsigned pmask = 0u;
+    __syncthreads();   // everyone has read line k-1's mirror, pivots and couplings
+    for (int i = tid; i < ROWS; i += nth) cNp[i] = cNn[i];
+    if (warp == 0) rg_eliminate<RL>(R, 0u, 0, b, lane, Xb, piv, &s_bad);
+    __syncthreads();
+    for (int P = 0; P < npan; ++P) {
+      const int w = min(8, b - 8 * P);
+      const c32* X = Xb + (P & 1) * 8 * ROWS;
+      // the panel's pivot rows leave the search
+      const unsigned before = pmask;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q < w) {
+          const int r = piv[8 * P + q];
+          if ((r & 31) == lane) pmask |= 1u << (r >> 5);
+        }
+      }
+      const unsigned fresh = pmask & ~before;
+      if (warp != P && has_cols) {
+        // old values of this strip (the T rows) through the warp's part of the mirror
+        c32* my = Mst + col0;
+#pragma unroll
+        for (int t = 0; t < RL; ++t) {
+          float4* dst = (float4*)(my + (lane + 32 * t) * LDC);
+#pragma unroll
+          for (int h = 0; h < 4; ++h) dst[h] = make_float4(R[t][2 * h].x, R[t][2 * h].y, R[t][2 * h + 1].x, R[t][2 * h + 1].y);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < RL; ++t)
+          if ((fresh >> t) & 1u)
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) R[t][jj] = mk<float>(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q >= w) break;
+          const float4* src = (const float4*)(my + piv[8 * P + q] * LDC);
+          c32 T[8];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float4 v = src[h];
+            T[2 * h] = mk<float>(v.x, v.y);
+            T[2 * h + 1] = mk<float>(v.z, v.w);
+          }
+#pragma unroll
+          for (int t = 0; t < RL; ++t) {
+            const c32 xv = X[q * ROWS + lane + 32 * t];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) cfma(R[t][jj], xv, T[jj]);
+          }
+        }
+        __syncwarp();
+      }
+      if (P + 1 < npan && warp == P + 1)
+        rg_eliminate<RL>(R, pmask, P + 1, b, lane, Xb + ((P + 1) & 1) * 8 * ROWS, piv, &s_bad);
+      __syncthreads();
+    }
+    // final strips to the mirror, and the inverse pivot map
+    if (has_cols) {
+      c32* my = Mst + col0;
+#pragma unroll
+      for (int t = 0; t < RL; ++t) {
+        float4* dst = (float4*)(my + (lane + 32 * t) * LDC);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) dst[h] = make_float4(R[t][2 * h].x, R[t][2 * h].y, R[t][2 * h + 1].x, R[t][2 * h + 1].y);
+      }
+    }
+    for (int c = tid; c < b; c += nth) rinv[piv[c]] = c;
+  }
+  if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
+}
+
 size_t factor_smem_bytes(int b, int ldb, int prec) {
   size_t el = prec == DDM_MIXED ? sizeof(c32) : sizeof(z64);
   (void)ldb;
   return (size_t)(b + FAC_W) * (32 * ((b + 31) / 32) + 1) * el + 6 * (size_t)b * el + 2 * (size_t)b * sizeof(int) + 64;
 }
 
-// All distinct factors in one launch, one CTA each.  d_reps[f] is a subdomain using factor
-// f, d_fofs[f] / d_ldb[f] its storage offset and leading dimension.
+// All distinct factors, one CTA each.  d_reps[f] is a subdomain using factor f, d_fofs[f] /
+// d_ldb[f] its storage offset and leading dimension.  complex64: the register-resident kernel,
+// one launch per block-width class (b <= 96: 12 warps, two CTAs per SM; b <= 128: 16 warps);
+// complex128: k_factor2d.
 cudaError_t launch_factor_all(ddm_ctx* c, const int* d_reps, const long long* d_fofs, const int* d_ldb) {
-  size_t sm = 0;
-  for (int f = 0; f < c->nfac; ++f) sm = std::max(sm, factor_smem_bytes(c->fac_b[f], c->fac_ldb[f], c->prec));
   cudaError_t e;
   if (c->prec == DDM_MIXED) {
-    e = allow_dynamic_smem((const void*)k_factor2d<float>, sm);
-    if (e != cudaSuccess) return e;
-    ++c->nlaunch;
-    k_factor2d<float><<<c->nfac, FAC_THREADS, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
-  } else {
-    e = allow_dynamic_smem((const void*)k_factor2d<double>, sm);
-    if (e != cudaSuccess) return e;
-    ++c->nlaunch;
-    k_factor2d<double><<<c->nfac, FAC_THREADS, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (z64*)c->d_G, c->d_err);
+    std::vector<int> sel;
+    int n3 = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int f = 0; f < c->nfac; ++f)
+        if ((c->fac_b[f] <= FacRG<3>::ROWS) == (pass == 0)) sel.push_back(f);
+    for (int f = 0; f < c->nfac; ++f) n3 += c->fac_b[f] <= FacRG<3>::ROWS ? 1 : 0;
+    if ((e = cudaMemcpyAsync(c->d_fsel, sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice, c->st)) !=
+        cudaSuccess)
+      return e;
+    if (n3 > 0) {
+      if ((e = allow_dynamic_smem((const void*)k_factor2d_rg<3>, FacRG<3>::smem())) != cudaSuccess) return e;
+      ++c->nlaunch;
+      k_factor2d_rg<3><<<n3, FacRG<3>::THREADS, FacRG<3>::smem(), c->st>>>(c->g, c->d_fsel, 0, d_reps, d_fofs, d_ldb,
+                                                                           (c32*)c->d_G, c->d_err);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (c->nfac > n3) {
+      if ((e = allow_dynamic_smem((const void*)k_factor2d_rg<4>, FacRG<4>::smem())) != cudaSuccess) return e;
+      ++c->nlaunch;
+      k_factor2d_rg<4><<<c->nfac - n3, FacRG<4>::THREADS, FacRG<4>::smem(), c->st>>>(
+          c->g, c->d_fsel, n3, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
+    }
+    return cudaGetLastError();
   }
+  size_t sm = 0;
+  for (int f = 0; f < c->nfac; ++f) sm = std::max(sm, factor_smem_bytes(c->fac_b[f], c->fac_ldb[f], c->prec));
+  e = allow_dynamic_smem((const void*)k_factor2d<double>, sm);
+  if (e != cudaSuccess) return e;
+  ++c->nlaunch;
+  k_factor2d<double><<<c->nfac, FAC_THREADS, sm, c->st>>>(c->g, d_reps, d_fofs, d_ldb, (z64*)c->d_G, c->d_err);
   return cudaGetLastError();
 }
 

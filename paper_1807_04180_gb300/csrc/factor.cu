@@ -282,80 +282,86 @@ __global__ void __launch_bounds__(FAC_THREADS, sizeof(T) == 4 ? 2 : 1) k_factor2
 // own columns as one rank-8 update,
 //     M[i][j] = [i not a pivot row of P] M[i][j] + sum_q X[i][q] T[q][j],
 // T[q][j] being the old value of pivot row r_q in column j.  T comes from the warp's own strip,
-// mirrored in shared memory once per panel.  Look-ahead: the owner of panel P + 1 applies panel
-// P's update to its strip and eliminates panel P + 1 while the other warps apply panel P, so each
-// panel costs one CTA barrier.  At the end of a line the strips go to shared memory.  The
+// mirrored in shared memory once per panel.  Look-ahead: the owner of panel P + 1 first applies
+// panel P's update to its strip (alone, so that it is not slowed by the others), signals the
+// other warps on a named barrier and eliminates panel P + 1 while they apply panel P; one CTA
+// barrier per panel.  The elimination of a panel is one block of straight-line code per pivot
+// (the pivot search is one warp max-reduction of the packed key), since this chain of 8 pivots
+// per panel bounds the kernel.  At the end of a line the strips go to shared memory.  The
 // permuted inverse is then written to global memory (column-major, as k_factor2d) and read back
 // for the next line's Schur complement.
-template <int RL>
+template <int RL, int NW = 4 * RL>
 struct FacRG {
-  static constexpr int ROWS = 32 * RL;        // rows held (b <= ROWS)
+  static constexpr int ROWS = 32 * RL;        // rows held
   static constexpr int LDC = ROWS + 2;        // row stride of the shared mirror (== 2 mod 16)
-  static constexpr int NWARP = ROWS / 8;      // column strips of 8
+  static constexpr int NWARP = NW;            // column strips of 8: b <= 8 NW
   static constexpr int THREADS = 32 * NWARP;
   static size_t smem() {
     return sizeof(c32) * ((size_t)ROWS * LDC + 2 * 8 * ROWS + 6 * ROWS) + 2 * sizeof(int) * ROWS;
   }
 };
 
-// Eliminate the 8 columns of panel pe held in R (rows lane + 32 t) with the rows flagged in pm
+// Eliminate the columns of panel pe held in R (rows lane + 32 t) with the rows flagged in pm
 // excluded from the pivot search; writes the panel's new columns to X (column-major, ROWS per
-// column) and its pivot rows to piv[8 pe + q].
-template <int RL>
+// column) and its pivot rows to piv[8 pe + q].  W = 8 for a full panel (the loop is one block of
+// straight-line code: no branch between the pivot steps); W = 0 takes the width from b.
+template <int RL, int W>
 __device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][8], unsigned pm, const int pe, const int b, const int lane,
                                              c32* X, int* piv, int* s_bad) {
   constexpr int ROWS = FacRG<RL>::ROWS;
-  const int w = min(8, b - 8 * pe);
+  const int w = W ? W : min(8, b - 8 * pe);
+  bool bad = false;
+  int rsel = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    if (q >= w) break;
+    if (!W && q >= w) break;
     // pivot: the unpivoted row of largest |M[r][c]|^2 (ties to the lowest row)
     unsigned key = 0u;
 #pragma unroll
     for (int t = 0; t < RL; ++t) {
       const int i = lane + 32 * t;
-      if (i < b && !((pm >> t) & 1u)) {
-        const unsigned kk = (__float_as_uint(cabs2(R[t][q])) & 0xFFFFFF00u) | (unsigned)(255 - i);
-        key = max(key, kk);
-      }
+      const unsigned kk = (__float_as_uint(cabs2(R[t][q])) & 0xFFFFFF00u) | (unsigned)(255 - i);
+      key = (i < b && !((pm >> t) & 1u)) ? max(key, kk) : key;
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+    key = __reduce_max_sync(0xffffffffu, key);
     const int r = key ? 255 - (int)(key & 0xFFu) : 0;
     const int tr = r >> 5, lr = r & 31;
-    // the pivot row's 8 values, from lane lr
     c32 sv[8];
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
+    for (int jo = 0; jo < 8; ++jo) {
+      const int jj = (q + jo) & 7;
       c32 v = R[0][jj];
 #pragma unroll
-      for (int t = 1; t < RL; ++t)
-        if (tr == t) v = R[t][jj];
+      for (int t = 1; t < RL; ++t) v = tr == t ? R[t][jj] : v;
       sv[jj].x = __shfl_sync(0xffffffffu, v.x, lr);
       sv[jj].y = __shfl_sync(0xffffffffu, v.y, lr);
     }
     const float pa = cabs2(sv[q]);
     const bool ok = key != 0u && pa > 0.f && isfinite(pa);
-    if (!ok && lane == 0) *s_bad = 1;
-    const c32 inv = ok ? cinv(sv[q]) : mk<float>(0.f, 0.f);
+    bad = bad || !ok;
+    const float rd = ok ? __frcp_rn(pa) : 0.f;
+    const c32 inv = mk<float>(sv[q].x * rd, -sv[q].y * rd);
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) sv[jj] = jj == q ? inv : sv[jj] * inv;
-    // row r becomes the scaled pivot row; every other row i loses f_i = M[i][c] times it, and
-    // its column c becomes -f_i / p
+    c32 nf[RL];
 #pragma unroll
-    for (int t = 0; t < RL; ++t) {
-      const bool isr = lane + 32 * t == r;
-      const c32 f = isr ? mk<float>(-1.f, 0.f) : R[t][q];
+    for (int t = 0; t < RL; ++t) nf[t] = lane + 32 * t == r ? mk<float>(1.f, 0.f) : -R[t][q];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
+    for (int jo = 1; jo <= 8; ++jo) {
+      const int jj = (q + jo) & 7;
+#pragma unroll
+      for (int t = 0; t < RL; ++t) {
+        const bool isr = lane + 32 * t == r;
         c32 base = (isr || jj == q) ? mk<float>(0.f, 0.f) : R[t][jj];
-        cfma(base, -f, sv[jj]);
+        cfma(base, nf[t], sv[jj]);
         R[t][jj] = base;
       }
     }
-    if (lane == lr) pm |= 1u << tr;
-    if (lane == 0) piv[8 * pe + q] = r;
+    pm |= lane == lr ? 1u << tr : 0u;
+    rsel = lane == q ? r : rsel;
   }
+  if (lane < w) piv[8 * pe + lane] = rsel;
+  if (bad && lane == 0) *s_bad = 1;
 #pragma unroll
   for (int t = 0; t < RL; ++t)
 #pragma unroll
@@ -363,10 +369,17 @@ __device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][8], unsigned pm, const
 }
 
 template <int RL>
-__global__ void __launch_bounds__(FacRG<RL>::THREADS, RL == 3 ? 2 : 1)
+__device__ __forceinline__ void rg_eliminate_any(c32 (&R)[RL][8], unsigned pm, const int pe, const int b,
+                                                 const int lane, c32* X, int* piv, int* s_bad) {
+  if (8 * pe + 8 <= b) rg_eliminate<RL, 8>(R, pm, pe, b, lane, X, piv, s_bad);
+  else rg_eliminate<RL, 0>(R, pm, pe, b, lane, X, piv, s_bad);
+}
+
+template <int RL, int NW>
+__global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
     k_factor2d_rg(Geom g, const int* fsel, int fsel_ofs, const int* reps, const long long* fofs_arr, const int* ldbs,
                   c32* Gout, int* err) {
-  constexpr int ROWS = FacRG<RL>::ROWS, LDC = FacRG<RL>::LDC;
+  constexpr int ROWS = FacRG<RL, NW>::ROWS, LDC = FacRG<RL, NW>::LDC;
   extern __shared__ __align__(16) unsigned char smem[];
   c32* Mst = (c32*)smem;                 // ROWS x LDC mirror of the strips (row-major)
   c32* Xb = Mst + ROWS * LDC;            // 2 x (8 columns x ROWS): published panel columns
@@ -407,9 +420,10 @@ __global__ void __launch_bounds__(FacRG<RL>::THREADS, RL == 3 ? 2 : 1)
     __syncthreads();   // line k's couplings; line k-1's final strips, pivots and rinv
     if (k > 0) {       // G_(k-1)[i][j] = M[r_i][rinv[j]], column j contiguous
       c32* Gk = Gout + fofs + (long long)(k - 1) * b * ldb;
-      for (int idx = tid; idx < b * ldb; idx += nth) {
-        const int j = idx / ldb, i = idx - j * ldb;
-        Gk[idx] = i < b ? Mst[piv[i] * LDC + rinv[j]] : mk<float>(0.f, 0.f);
+      for (int j = warp; j < b; j += nth >> 5) {
+        const int cj = rinv[j];
+        for (int i = lane; i < ldb; i += 32)
+          Gk[(long long)j * ldb + i] = i < b ? Mst[piv[i] * LDC + cj] : mk<float>(0.f, 0.f);
       }
     }
     if (k == m) break;
@@ -433,21 +447,24 @@ __global__ void __launch_bounds__(FacRG<RL>::THREADS, RL == 3 ? 2 : 1)
     unsigned pmask = 0u;
     __syncthreads();   // everyone has read line k-1's mirror, pivots and couplings
     for (int i = tid; i < ROWS; i += nth) cNp[i] = cNn[i];
-    if (warp == 0) rg_eliminate<RL>(R, 0u, 0, b, lane, Xb, piv, &s_bad);
+    if (warp == 0) rg_eliminate_any<RL>(R, 0u, 0, b, lane, Xb, piv, &s_bad);
     __syncthreads();
     for (int P = 0; P < npan; ++P) {
       const int w = min(8, b - 8 * P);
       const c32* X = Xb + (P & 1) * 8 * ROWS;
       // the panel's pivot rows leave the search
+      int rq[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) rq[q] = q < w ? piv[8 * P + q] : piv[8 * P];
       const unsigned before = pmask;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q < w) {
-          const int r = piv[8 * P + q];
-          if ((r & 31) == lane) pmask |= 1u << (r >> 5);
-        }
-      }
+      for (int q = 0; q < 8; ++q) pmask |= (q < w && (rq[q] & 31) == lane) ? 1u << (rq[q] >> 5) : 0u;
       const unsigned fresh = pmask & ~before;
+      // the owner of the next panel updates its strip first, then signals (named barrier 1) and
+      // eliminates; the other warps update theirs after the signal, beside the elimination
+      const bool ahead = P + 1 < npan;
+      const bool owner_next = ahead && warp == P + 1;
+      if (ahead && !owner_next) asm volatile("bar.sync 1, %0;" ::"r"(nth) : "memory");
       if (warp != P && has_cols) {
         // old values of this strip (the T rows) through the warp's part of the mirror
         c32* my = Mst + col0;
@@ -460,13 +477,12 @@ __global__ void __launch_bounds__(FacRG<RL>::THREADS, RL == 3 ? 2 : 1)
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < RL; ++t)
-          if ((fresh >> t) & 1u)
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) R[t][jj] = mk<float>(0.f, 0.f);
+          for (int jj = 0; jj < 8; ++jj) R[t][jj] = ((fresh >> t) & 1u) ? mk<float>(0.f, 0.f) : R[t][jj];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          if (q >= w) break;
-          const float4* src = (const float4*)(my + piv[8 * P + q] * LDC);
+          // q >= w (a partial last panel): X[q] is zero there, the product adds nothing
+          const float4* src = (const float4*)(my + rq[q] * LDC);
           c32 T[8];
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
@@ -483,8 +499,10 @@ __global__ void __launch_bounds__(FacRG<RL>::THREADS, RL == 3 ? 2 : 1)
         }
         __syncwarp();
       }
-      if (P + 1 < npan && warp == P + 1)
-        rg_eliminate<RL>(R, pmask, P + 1, b, lane, Xb + ((P + 1) & 1) * 8 * ROWS, piv, &s_bad);
+      if (owner_next) {
+        asm volatile("bar.arrive 1, %0;" ::"r"(nth) : "memory");
+        rg_eliminate_any<RL>(R, pmask, P + 1, b, lane, Xb + ((P + 1) & 1) * 8 * ROWS, piv, &s_bad);
+      }
       __syncthreads();
     }
     // final strips to the mirror, and the inverse pivot map
@@ -512,32 +530,31 @@ size_t factor_smem_bytes(int b, int ldb, int prec) {
 // d_ldb[f] its storage offset and leading dimension.  complex64: the register-resident kernel,
 // one launch per block-width class (b <= 96: 12 warps, two CTAs per SM; b <= 128: 16 warps);
 // complex128: k_factor2d.
+template <int RL, int NW>
+static cudaError_t launch_rg(ddm_ctx* c, int n, int ofs, const int* d_reps, const long long* d_fofs, const int* d_ldb) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = allow_dynamic_smem((const void*)k_factor2d_rg<RL, NW>, FacRG<RL, NW>::smem());
+  if (e != cudaSuccess) return e;
+  ++c->nlaunch;
+  k_factor2d_rg<RL, NW><<<n, FacRG<RL, NW>::THREADS, FacRG<RL, NW>::smem(), c->st>>>(
+      c->g, c->d_fsel, ofs, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_factor_all(ddm_ctx* c, const int* d_reps, const long long* d_fofs, const int* d_ldb) {
   cudaError_t e;
   if (c->prec == DDM_MIXED) {
+    // width classes: b <= 96 (12 warps, two CTAs per SM), b <= 128 (16 warps, one CTA per SM)
     std::vector<int> sel;
-    int n3 = 0;
-    for (int pass = 0; pass < 2; ++pass)
+    int cnt[2] = {0, 0};
+    for (int k = 0; k < 2; ++k)
       for (int f = 0; f < c->nfac; ++f)
-        if ((c->fac_b[f] <= FacRG<3>::ROWS) == (pass == 0)) sel.push_back(f);
-    for (int f = 0; f < c->nfac; ++f) n3 += c->fac_b[f] <= FacRG<3>::ROWS ? 1 : 0;
+        if ((c->fac_b[f] > 96) == (k == 1)) { sel.push_back(f); ++cnt[k]; }
     if ((e = cudaMemcpyAsync(c->d_fsel, sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice, c->st)) !=
         cudaSuccess)
       return e;
-    if (n3 > 0) {
-      if ((e = allow_dynamic_smem((const void*)k_factor2d_rg<3>, FacRG<3>::smem())) != cudaSuccess) return e;
-      ++c->nlaunch;
-      k_factor2d_rg<3><<<n3, FacRG<3>::THREADS, FacRG<3>::smem(), c->st>>>(c->g, c->d_fsel, 0, d_reps, d_fofs, d_ldb,
-                                                                           (c32*)c->d_G, c->d_err);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (c->nfac > n3) {
-      if ((e = allow_dynamic_smem((const void*)k_factor2d_rg<4>, FacRG<4>::smem())) != cudaSuccess) return e;
-      ++c->nlaunch;
-      k_factor2d_rg<4><<<c->nfac - n3, FacRG<4>::THREADS, FacRG<4>::smem(), c->st>>>(
-          c->g, c->d_fsel, n3, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
-    }
-    return cudaGetLastError();
+    if ((e = launch_rg<3, 12>(c, cnt[0], 0, d_reps, d_fofs, d_ldb)) != cudaSuccess) return e;
+    return launch_rg<4, 16>(c, cnt[1], cnt[0], d_reps, d_fofs, d_ldb);
   }
   size_t sm = 0;
   for (int f = 0; f < c->nfac; ++f) sm = std::max(sm, factor_smem_bytes(c->fac_b[f], c->fac_ldb[f], c->prec));

@@ -593,6 +593,53 @@ def run_serve(args):
                        "slots": args.serve_slots, "budget": "80% of free HBM", "admission": "hrrn"}}
 
 
+def run_table3(args):
+    """The paper's iterative-solver experiments (Section 4.2.1) at the paper's sizes on one GPU:
+    N x N subdomains of 300^2 own nodes + a 30-node overlap/PML band (b = 360), Algorithm 3.1 as
+    an iterative solver to a relative residual of 1e-8.  Table 3 (constant medium, one shared
+    factor): N = 2 .. 64 in mixed precision (complex64 local solves on the tensor cores, FP64
+    refinement) and N <= 8 in FP64 (the paper's arithmetic; its step counts are comparable one to
+    one).  Table 4 (the seeded layered stand-in, every subdomain its own factor): N <= 16 in mixed
+    precision.  One JSON line with n_DDM_iter, n_DDM_solve = n_iter / (N1 + N2) and the times
+    beside the paper's counts."""
+    import torch
+    from paper_1807_04180_gb300 import ddm as D
+    with open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")) as fh:
+        gold = json.load(fh)
+    rows = []
+    plan = [("constant", N, D.DDM_MIXED) for N in args.table3_parts] + \
+           [("constant", N, D.DDM_FP64) for N in args.table3_parts if N <= 8] + \
+           [("layered", N, D.DDM_MIXED) for N in args.table3_parts if N <= 8]
+    for medium, N, prec in plan:
+        wl = W.paper_table3(N, medium)
+        t0 = time.perf_counter()
+        s = D.Solver(wl, precision=prec)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        s.factor()
+        u = torch.zeros(wl.c.shape, dtype=torch.complex128, device="cuda")
+        info = D.ddm_solve(s.ctx, s.to_dev(wl.f[0]), u, tol=1e-8, max_it=60 * N, mode=D.DDM_STEPPING, check=False)
+        torch.cuda.synchronize()
+        key = "table3_const_iters" if medium == "constant" else "table4_layered_iters"
+        pi = gold[key]["parts"].index(N) if N in gold[key]["parts"] else None
+        rows.append({"table": 3 if medium == "constant" else 4, "parts": N, "mesh": wl.n[0],
+                     "omega_over_2pi": wl.omega / (2 * math.pi), "precision": "mixed" if prec == D.DDM_MIXED else "fp64",
+                     "n_ddm_iter": info["ddm_steps"], "n_ddm_solve": info["ddm_steps"] / (2 * N),
+                     "paper_n_ddm_iter": gold[key]["n_iter"][pi] if pi is not None else None,
+                     "converged": bool(info["converged"]), "rel_residual": info["rel_residual"],
+                     "n_unique_factors": info["n_unique_factors"], "setup_s": t_setup,
+                     "factor_ms": info["factor_ms"], "solve_ms": info["solve_ms"],
+                     "ms_per_ddm_step": info["solve_ms"] / max(info["ddm_steps"], 1)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        s.close()
+        del u
+        torch.cuda.empty_cache()
+    return {"metric": "Tables 3-4 at the paper's sizes: DDM steps to 1e-8 and time per step (one GPU)",
+            "rows": rows, "data": "synthetic",
+            "config": {"workload": "paper_table3: N x N subdomains of 300^2 + 30-node overlap/PML, tol 1e-8, "
+                                   "stepping solver", "parts": args.table3_parts}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -609,6 +656,9 @@ def main():
     ap.add_argument("--no-extra-configs", action="store_true",
                     help="headline line only (no 2048^2 batched, 192^3 and serving keys)")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (p50/p99 latency), one JSON line")
+    ap.add_argument("--table3", action="store_true",
+                    help="the paper's Tables 3-4 at the paper's subdomain size (b = 360), one JSON line")
+    ap.add_argument("--table3-parts", type=int, nargs="+", default=[2, 4, 8, 16, 32, 64])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--workload", choices=["heterogeneous_2d", "layered_2d_batched", "constant_3d"],
@@ -639,6 +689,10 @@ def main():
     if args.serve:
         if rank == 0:
             print(json.dumps(run_serve(args)))
+        return
+    if args.table3:
+        if rank == 0:
+            print(json.dumps(run_table3(args)))
         return
     if args.workload != "heterogeneous_2d":
         out = run_workload(args.workload, args.steps, args.warmup, args.max_it, rank, world, local_rank)

@@ -124,7 +124,11 @@ ddm_status ddm_set_medium_host(ddm_ctx *ctx, double omega, const double *c_host)
  * tridiagonal LU in explicit-inverse form: G_k = D_k^{-1} with
  * D_k = T_k - L_k G_{k-1} U_{k-1} over the x-lines (2D) or z-planes (3D) of
  * the subdomain, each D_k inverted by Gauss-Jordan with partial pivoting
- * inside the block (in shared memory in 2D, in global memory in 3D).
+ * inside the block: in registers / shared memory in 2D when the x-lines are
+ * at most 128 nodes (complex64) or 96 (complex128) wide, otherwise (wider
+ * 2D subdomains such as the paper's 300^2 + PML, and every 3D partition) as
+ * dense blocks in global memory, each block step of the local solves then a
+ * contraction over all subdomains and right-hand sides sharing a factor.
  * Errors: DDM_E_SINGULAR if a pivot fell below 1e-30 relative to its column,
  * DDM_E_CUDA, DDM_E_STATE.                                                  */
 ddm_status ddm_factor(ddm_ctx *ctx);
@@ -160,8 +164,9 @@ ddm_status ddm_solve_host(ddm_ctx *ctx, const void *f_host, void *u_host, int nr
  * batched local solves, K-1 transfers, assembly -- captured on the first use
  * of each (nrhs, K) on a library-owned non-blocking stream and ordered with
  * the context's stream by events.  Inputs and outputs pass through staging
- * vectors held by the context.  0 turns it off.  2D partitions only.
- * Errors: DDM_E_INVAL (3D).                                                  */
+ * vectors held by the context.  0 turns it off.  2D partitions on the 2D
+ * kernels only (x-lines of at most 128 / 96 nodes, see ddm_factor).
+ * Errors: DDM_E_INVAL (3D, or wider 2D subdomains).                          */
 ddm_status ddm_set_graph(ddm_ctx *ctx, int enable);
 
 /* Block solves of Algorithm 3.1 on the tensor cores (DDM_MIXED only).  In 3D

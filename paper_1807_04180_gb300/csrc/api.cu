@@ -127,10 +127,14 @@ extern "C" ddm_status ddm_setup(const ddm_params* p, double omega, const double*
     for (int i = 0; i < p->parts[a]; ++i) {
       int64_t w = c->cuts_h[a][i + 1] - c->cuts_h[a][i];
       if (w < 2 * ov || w < 2) { delete c; return fail(nullptr, DDM_E_INVAL, "every part must be at least 2*overlap nodes wide"); }
-      if (d == 2 && a == 0 && w + 2 * e > 128) { delete c; return fail(nullptr, DDM_E_INVAL, "x-extent of a 2D subdomain (own + 2(overlap+pml)) must be <= 128"); }
+      if (d == 2 && a == 0 && w + 2 * e > 1024) { delete c; return fail(nullptr, DDM_E_INVAL, "x-extent of a 2D subdomain (own + 2(overlap+pml)) must be <= 1024"); }
+      // the 2D kernels keep a block in shared memory / registers: up to 128 nodes in complex64,
+      // 96 in complex128; wider x-lines take the dense-block path
+      if (d == 2 && a == 0 && w + 2 * e > (p->precision == DDM_MIXED ? 128 : 96)) c->blockpath = true;
       if (d == 3 && a < 2 && w + 2 * e > 96) { delete c; return fail(nullptr, DDM_E_INVAL, "x- and y-extents of a 3D subdomain must be <= 96"); }
     }
   }
+  if (d == 3) c->blockpath = true;
   g.nglob = (long long)g.N[0] * g.N[1] * g.N[2];
   // alpha tables: one per (axis, part), then the global box per axis
   std::vector<int> tdesc;
@@ -440,7 +444,7 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   cudaEventRecord(e0, c->st);
   {
     TScope ts(c, T_FACTOR);
-    if (c->dim == 2) {
+    if (!c->blockpath) {
       CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
       if (c->prec == DDM_MIXED && c->p.max_rhs >= 16) CK(tc2d_pack_factors(c));
     }
@@ -932,7 +936,8 @@ extern "C" ddm_status ddm_timing(ddm_ctx* c, int enable, int reset, double* out_
 
 extern "C" ddm_status ddm_set_graph(ddm_ctx* c, int enable) {
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
-  if (enable && c->dim != 2) return fail(c, DDM_E_INVAL, "graph replay of M_K is implemented for 2D partitions");
+  if (enable && c->blockpath)
+    return fail(c, DDM_E_INVAL, "graph replay of M_K is implemented for 2D partitions of subdomains at most 128 nodes wide");
   c->use_graph = enable != 0;
   return DDM_OK;
 }
@@ -980,6 +985,8 @@ extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int6
   }
   // local length and factor storage (every subdomain distinct: the upper bound)
   long long lsum = 0, tcfac = 0, tcy = 0;
+  bool anywide = false;   // a 2D partition with x-lines wider than 128 runs on the block path
+  if (d == 2) for (long long wx : widths[0]) anywide = anywide || wx > (p->precision == DDM_MIXED ? 128 : 96);
   std::vector<long long> s1 = widths[0], s2 = d > 1 ? widths[1] : std::vector<long long>{1},
                          s3 = d > 2 ? widths[2] : std::vector<long long>{1};
   for (long long wz : s3)
@@ -988,8 +995,9 @@ extern "C" ddm_status ddm_workspace_bytes(const ddm_params* p, int restart, int6
         lsum += wx * wy * wz;
         const long long b = d == 2 ? wx : wx * wy, m = d == 2 ? wy : wz, ldb = (b + 3) & ~3LL;
         fac += m * b * ldb;
-        if (d == 2 && p->precision == DDM_MIXED && p->max_rhs >= 16) tcfac += 4 * tc2d_packed_floats((int)b, (int)m);
-        if (d == 3 && p->precision == DDM_MIXED) {
+        const bool block = d == 3 || anywide;
+        if (!block && p->precision == DDM_MIXED && p->max_rhs >= 16) tcfac += 4 * tc2d_packed_floats((int)b, (int)m);
+        if (block && p->precision == DDM_MIXED) {
           tcfac += 4 * tc3d_packed_floats((int)b, (int)m);
           tcy = std::max(tcy, 4 * tc3d_packed_floats((int)b, 1) / std::max(1LL, (b + 127) / 128));
         }
@@ -1028,7 +1036,7 @@ extern "C" ddm_status ddm_factor_bytes(const ddm_ctx* c, int64_t* per_solve, int
   if (!c || !c->factored) return DDM_E_STATE;
   const long long el = (long long)local_elem(c);
   long long ps = 0;
-  if (c->dim == 2) {
+  if (!c->blockpath) {
     for (auto& s : c->subs) {
       long long b = s.ext[0], m = s.ext[1];
       ps += (2 * m - 1) * b * b * el;

@@ -31,27 +31,31 @@ template <typename T>
 __global__ void k_f3_schur(Geom g, int rep, const cplx<T>* G, long long fofs, int ldb, int k, cplx<T>* W, int ldw,
                            const int* cm) {
   const SubDesc& s = g.subs[rep];
-  const int ex = s.ext[0], ey = s.ext[1], ez = s.ext[2];
+  // 3D: blocks are z-planes (in-plane x and y couplings); 2D (subdomains wider than the 2D
+  // kernels take): blocks are x-lines (x couplings only), coupled along y
+  const int d = g.dim;
+  const int ex = s.ext[0], ey = d == 3 ? s.ext[1] : 1, nb = s.ext[d - 1];
   const int b = ex * ey;
-  const long long len = (long long)b * ez;
-  const cplx<T>* lc = (const cplx<T>*)g.lcoef + s.vofs * 7;   // C, x-, x+, y-, y+, z-, z+
+  const long long len = (long long)b * nb;
+  const int zm = 2 * d - 1, zp = 2 * d;   // planes of the couplings to the previous / next block
+  const cplx<T>* lc = (const cplx<T>*)g.lcoef + s.vofs * (2 * d + 1);   // C, x-, x+, y-, y+(, z-, z+)
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)b * b;
        idx += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(idx / b), j = (int)(idx - (long long)i * b);
-    cplx<T> d = mk<T>(0, 0);
+    cplx<T> dv = mk<T>(0, 0);
     const long long oi = (long long)k * b + i;
     if (k > 0) {
       const cplx<T> gij = G[fofs + ((long long)(k - 1) * b + j) * ldb + i];
       const long long oj = (long long)(k - 1) * b + j;
-      d = -(lc[5 * len + oi] * gij * lc[6 * len + oj]);
+      dv = -(lc[zm * len + oi] * gij * lc[zp * len + oj]);
     }
-    if (j == i) d = d + lc[oi];
+    if (j == i) dv = dv + lc[oi];
     const int xi = i % ex, yi = i / ex;
-    if (j == i + 1 && xi + 1 < ex) d = d + lc[2 * len + oi];
-    if (j == i - 1 && xi > 0) d = d + lc[1 * len + oi];
-    if (j == i + ex && yi + 1 < ey) d = d + lc[4 * len + oi];
-    if (j == i - ex && yi > 0) d = d + lc[3 * len + oi];
-    W[(long long)i * ldw + j] = d;
+    if (j == i + 1 && xi + 1 < ex) dv = dv + lc[2 * len + oi];
+    if (j == i - 1 && xi > 0) dv = dv + lc[1 * len + oi];
+    if (d == 3 && j == i + ex && yi + 1 < ey) dv = dv + lc[4 * len + oi];
+    if (d == 3 && j == i - ex && yi > 0) dv = dv + lc[3 * len + oi];
+    W[(long long)i * ldw + j] = dv;
   }
   (void)cm;
 }
@@ -586,10 +590,11 @@ static cudaError_t solve3d_t(ddm_ctx* c, const void* src, void* out, void* U, in
     const SubDesc& s = c->subs[rep[f]];
     const int b = c->fac_b[f], m = c->fac_m[f], ldb = c->fac_ldb[f];
     const long long len = (long long)b * m;
-    const cplx<T>* lc = (const cplx<T>*)c->d_lcoef + s.vofs * 7;
+    const int zm = 2 * c->dim - 1, zp = 2 * c->dim;   // couplings to the previous / next block
+    const cplx<T>* lc = (const cplx<T>*)c->d_lcoef + s.vofs * (2 * c->dim + 1);
     if constexpr (std::is_same<T, float>::value) {
       if (c->use_tc && c->d_gtc) {
-        if ((e = tc3d_sweeps(c, f, c->d_col3d, ncol, lc + 5 * len, lc + 6 * len, (const c32*)src, (c32*)out,
+        if ((e = tc3d_sweeps(c, f, c->d_col3d, ncol, lc + zm * len, lc + zp * len, (const c32*)src, (c32*)out,
                              (c32*)U)) != cudaSuccess)
           return e;
         if (f + 1 < c->nfac) cudaStreamSynchronize(c->st);
@@ -601,7 +606,7 @@ static cudaError_t solve3d_t(ddm_ctx* c, const void* src, void* out, void* U, in
       const int pass = i < m ? 0 : 1;
       const int k = pass == 0 ? i : 2 * m - 2 - i;
       ++c->nlaunch;
-      k_gemm3d<T><<<grid, 256, 0, c->st>>>((const cplx<T>*)c->d_G, c->fac_ofs[f], ldb, b, lc + 5 * len, lc + 6 * len,
+      k_gemm3d<T><<<grid, 256, 0, c->st>>>((const cplx<T>*)c->d_G, c->fac_ofs[f], ldb, b, lc + zm * len, lc + zp * len,
                                            pass, k, m, c->d_col3d, ncol, (const cplx<T>*)src, (cplx<T>*)out,
                                            (cplx<T>*)U);
     }

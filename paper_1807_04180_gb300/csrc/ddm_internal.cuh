@@ -156,6 +156,9 @@ struct ddm_ctx {
   double omega;
   cudaStream_t st;
   int dim, e, prec;
+  // block path: the subdomain factors and solves run on the dense-block machinery (3D z-planes;
+  // in 2D when some subdomain's x-lines are wider than the 2D kernels' 128 nodes)
+  bool blockpath = false;
   ddm::Geom g;
   std::vector<ddm::SubDesc> subs;
   ddm::SubDesc* d_subs = nullptr;

@@ -291,3 +291,35 @@ def constant_3d(n: int = 192, parts: int = 8, ov: int = 1, npml: int = 6, k_over
     f = gaussian_source(shape, h, e, center, 2 * h)[None]
     return Workload(f"3d-constant-{n}", shape, h, (uniform_cuts(n, parts),) * 3, ov, npml, 50.0, 2.0, k,
                     constant_medium(shape, e), f, tol=1e-6, K=2)
+
+
+# Table 3: omega / 2 pi for N x N subdomains of 300^2 (5 + 25 N: 55, 105, 205, 405, 805, 1605)
+TABLE3_FREQ = {2: 55.0, 4: 105.0, 8: 205.0, 16: 405.0, 32: 805.0, 64: 1605.0}
+# Table 4 (layered medium): 27.5, 52.5, 102.5, ...
+TABLE4_FREQ = {2: 27.5, 4: 52.5, 8: 102.5, 16: 202.5, 32: 402.5, 64: 802.5}
+
+
+def paper_table3(N: int, medium: str = "constant", seed: int = 6, ov: int = 2, npml: int = 28) -> Workload:
+    """The paper's iterative-solver experiments (Section 4.2.1, Tables 3-4): N x N subdomains of
+    300^2 own nodes on [0, 1]^2 (h = 1 / (300 N)), each extended by overlap + PML = 30 nodes per
+    side (b = 360 nodes per x-line), omega / 2 pi from the tables (about 11 points per
+    wavelength at c = 1), a single-shot source at (x0 + dxi / 4, y0 + deta / 3) of the first
+    subdomain, tolerance 1e-8.  medium "constant": c = 1 (Table 3); "layered": the seeded
+    6-layer stand-in for the paper's 5-layer model (Table 4's frequencies, c in [1, 3] so that the
+    slowest layer keeps the table's points per wavelength; the model itself exists only as a
+    figure)."""
+    n = 300 * N
+    h = 1.0 / n
+    e = ov + npml
+    if medium == "constant":
+        c = constant_medium((n, n), e, 1.0)
+        omega = 2 * math.pi * TABLE3_FREQ[N]
+    elif medium == "layered":
+        c = layered_medium((n, n), h, e, seed, cmin=1.0, cmax=3.0)
+        omega = 2 * math.pi * TABLE4_FREQ[N]
+    else:
+        raise ValueError("medium must be 'constant' or 'layered'")
+    pos = ((300 / 3.0) * h, (300 / 4.0) * h)       # (y, x): y0 + deta/3, x0 + dxi/4
+    f = point_source((n, n), h, e, pos)[None]
+    return Workload(f"2d-table3-{medium}-{N}x{N}", (n, n), h, (uniform_cuts(n, N),) * 2, ov, npml, 50.0, 2.0,
+                    omega, c, f, tol=1e-8, K=2)

@@ -333,6 +333,7 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
                   c->d_gtc, c->d_ytc, c->d_tcpart, c->d_gtc2, c->d_tc2ofs, c->d_hash, c->d_pairs, c->d_mis,
                   c->d_reps, c->d_ldb, c->d_fofs, c->d_fsel, c->d_coef};
   for (void* q : ptrs) dev_free(c, q);
+  for (auto& pl : c->tc2plans) { dev_free(c, pl.second.d_ofs); dev_free(c, pl.second.d_items); }
   cudaStreamSynchronize(c->st);   // the frees are stream-ordered: complete them before returning
   host_pinned_free(c->h_scal);
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }

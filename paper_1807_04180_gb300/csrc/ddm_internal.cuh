@@ -225,6 +225,11 @@ struct ddm_ctx {
   long long* d_tc2ofs = nullptr;
   size_t gtc2_cap = 0, tc2ofs_cap = 0;   // floats, entries
   std::vector<long long> tc2_ofs;
+  // persistent tensor-core solve: per number of 64-right-hand-side groups, the CTA count and the
+  // device arrays of the work lists (CTA i runs items[ofs[i] .. ofs[i+1])), built once outside
+  // any graph capture and kept until the context is destroyed
+  struct TC2Plan { int nctas = 0; int* d_ofs = nullptr; int2* d_items = nullptr; };
+  std::map<int, TC2Plan> tc2plans;
   // autotuned right-hand sides per CTA of the 2D local solve, per nrhs, and the timings taken
   std::map<int, int> tuned_nr;
   int forced_nr = 0;             // ddm_set_rhs_per_cta: 0 = autotuned

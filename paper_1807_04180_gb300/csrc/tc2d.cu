@@ -114,9 +114,36 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// One work item of the persistent solve: subdomain s and its right-hand-side group starting at r0.
+struct TC2Item {
+  const SubDesc* s;
+  int b, m, ng, bp, nKC, nblk, r0, nr;
+  uint32_t stage;   // bytes of one chunk of this subdomain's factor (2 planes x 2 ng row groups)
+};
+__device__ __forceinline__ TC2Item tc2_item(const Geom& g, int2 it, int nrhs) {
+  TC2Item I;
+  I.s = &g.subs[it.x];
+  I.b = I.s->ext[0];
+  I.m = I.s->ext[1];
+  I.ng = (I.b + 7) / 8;
+  I.bp = 8 * I.ng;
+  I.nKC = (I.b + TC2_KC - 1) / TC2_KC;
+  I.nblk = 2 * I.m - 1;
+  I.r0 = it.y * TC2_NRT;
+  I.nr = min(TC2_NRT, nrhs - I.r0);
+  I.stage = 512u * TC2_KCC * (uint32_t)I.ng;
+  return I;
+}
+
+// Persistent: CTA i runs the work items items[cta_ofs[i] .. cta_ofs[i + 1]) in order (the host
+// deals the (subdomain, right-hand-side group) items out longest first to the least loaded CTA).
+// Tensor memory and the barriers are set up once; the stage ring (slots of the widest subdomain's
+// chunk) and the barrier phases run on across items, so the producer streams the next item's
+// factor while the epilogue finishes the current one.
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_solve2d_tc(Geom g, const float* __restrict__ gtc, const long long* __restrict__ tcofs,
-                 const c32* __restrict__ src, c32* out, int nrhs, int nst, int* err) {
+                 const c32* __restrict__ src, c32* out, int nrhs, int nst, int ngmax,
+                 const int* __restrict__ cta_ofs, const int2* __restrict__ items, int* err) {
   extern __shared__ unsigned char smem_raw[];
   // s_raw: a stage's FP32 plane has landed (bulk copy); s_full: its hi / lo planes are written
   __shared__ __align__(8) uint64_t s_raw[TC2_MAXST], s_full[TC2_MAXST], s_empty[TC2_MAXST], s_yfull, s_dfull;
@@ -128,14 +155,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   __shared__ __align__(16) c32 s_xpose[TC2_NEPI][8 * 18];
   volatile int* abort_flag = &s_abort;
 
-  // the right-hand-side groups of one subdomain are adjacent in launch order, so that they run
-  // at the same time and the second read of each factor block hits L2
-  const SubDesc& s = g.subs[blockIdx.y];
-  const int b = s.ext[0], m = s.ext[1];
-  const int ng = (b + 7) / 8, bp = 8 * ng, nKC = (b + TC2_KC - 1) / TC2_KC;
-  const int nblk = 2 * m - 1;
-  const int r0 = blockIdx.x * TC2_NRT, nr = min(TC2_NRT, nrhs - r0);
-  const uint32_t STAGE = 512u * TC2_KCC * (uint32_t)ng;     // one chunk: 2 planes x 2 ng groups
+  const int it0 = cta_ofs[blockIdx.x], it1 = cta_ofs[blockIdx.x + 1];
+  const uint32_t SSTRIDE = 512u * TC2_KCC * (uint32_t)ngmax;   // ring slot: the widest chunk
   const uint32_t raw = tc::smem_addr(smem_raw);
   const uint32_t ring = (raw + 127u) & ~127u;
 
@@ -169,21 +190,27 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   if (warp == TC2_NEPI) {
     // ------------------------------------------------------------------ producer
     if (lane == 0) {
-      const float* gsrc = gtc + tcofs[s.fid];
       long long c = 0;
-      for (int bi = 0; bi < nblk && !*abort_flag; ++bi) {
-        int pass, k;
-        seq2(bi, m, pass, k);
-        for (int kc = 0; kc < nKC; ++kc, ++c) {
-          const int st = (int)(c % nst);
-          if (c >= nst && !tc::bar_wait_or_abort(tc::smem_addr(&s_empty[st]), (uint32_t)((c / nst) - 1) & 1u,
-                                                   abort_flag)) {
-            atomicOr(err, ERRBIT_TIMEOUT);
-            break;
+      bool ok = true;
+      for (int ii = it0; ii < it1 && ok; ++ii) {
+        const TC2Item I = tc2_item(g, items[ii], nrhs);
+        const float* gsrc = gtc + tcofs[I.s->fid];
+        for (int bi = 0; bi < I.nblk && ok && !*abort_flag; ++bi) {
+          int pass, k;
+          seq2(bi, I.m, pass, k);
+          for (int kc = 0; kc < I.nKC; ++kc, ++c) {
+            const int st = (int)(c % nst);
+            if (c >= nst && !tc::bar_wait_or_abort(tc::smem_addr(&s_empty[st]), (uint32_t)((c / nst) - 1) & 1u,
+                                                     abort_flag)) {
+              atomicOr(err, ERRBIT_TIMEOUT);
+              ok = false;
+              break;
+            }
+            const uint32_t fb = tc::smem_addr(&s_raw[st]);
+            tc::bar_expect_tx(fb, I.stage / 2);
+            tc::bulk_load(ring + (uint32_t)st * SSTRIDE, gsrc + ((long long)k * I.nKC + kc) * (I.stage / 8),
+                          I.stage / 2, fb);
           }
-          const uint32_t fb = tc::smem_addr(&s_raw[st]);
-          tc::bar_expect_tx(fb, STAGE / 2);
-          tc::bulk_load(ring + (uint32_t)st * STAGE, gsrc + ((long long)k * nKC + kc) * (STAGE / 8), STAGE / 2, fb);
         }
       }
       // the copies still in flight land before the CTA may exit (bounded)
@@ -193,24 +220,26 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
   } else if (warp == TC2_NEPI + 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t ID = tc::idesc_tf32(128, 2 * bp, false);
       // descriptor at the first stage and K step; others only move the start address (>> 4)
       const uint64_t dB = tc::sdesc(ring, 128, 128 * TC2_KCC);
-      const uint64_t BLO = (uint64_t)(STAGE / 2) >> 4;     // lo plane of a stage
-      const int nks = (b + 7) / 8;                          // K steps that are not all padding
-      long long c = 0;
+      long long c = 0, gbi = 0;   // chunks and blocks over all items so far
       bool ok = true;
-      for (int bi = 0; bi < nblk && ok; ++bi) {
-        if (!tc::bar_spin_or_abort(tc::smem_addr(&s_yfull), (uint32_t)(bi & 1), abort_flag)) { ok = false; break; }
+      for (int ii = it0; ii < it1 && ok; ++ii) {
+      const TC2Item I = tc2_item(g, items[ii], nrhs);
+      const uint32_t ID = tc::idesc_tf32(128, 2 * I.bp, false);
+      const uint64_t BLO = (uint64_t)(I.stage / 2) >> 4;   // lo plane of a stage
+      const int nks = (I.b + 7) / 8;                       // K steps that are not all padding
+      for (int bi = 0; bi < I.nblk && ok; ++bi, ++gbi) {
+        if (!tc::bar_spin_or_abort(tc::smem_addr(&s_yfull), (uint32_t)(gbi & 1), abort_flag)) { ok = false; break; }
         tc::fence_after();
-        for (int kc = 0; kc < nKC; ++kc, ++c) {
+        for (int kc = 0; kc < I.nKC; ++kc, ++c) {
           const int st = (int)(c % nst);
           if (!tc::bar_spin_or_abort(tc::smem_addr(&s_full[st]), (uint32_t)((c / nst) & 1), abort_flag)) {
             ok = false;
             break;
           }
           tc::fence_after();
-          const uint64_t bst = dB + (((uint64_t)st * STAGE) >> 4);
+          const uint64_t bst = dB + (((uint64_t)st * SSTRIDE) >> 4);
 #pragma unroll
           for (int t = 0; t < TC2_KSTEPS; ++t) {
             const int ks = TC2_KSTEPS * kc + t;
@@ -227,6 +256,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         if (!ok) break;
         tc::mma_commit(tc::smem_addr(&s_dfull));
       }
+      }
       if (!ok) atomicOr(err, ERRBIT_TIMEOUT);
     }
   } else if (warp >= TC2_NEPI + 2) {
@@ -235,11 +265,13 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     // its lo part goes to plane 1 (x = hi + lo exactly); the generic-proxy writes are fenced for
     // the tensor core before s_full is signalled.
     const int st_tid = tid - (TC2_NEPI + 2) * 32;
-    const int n4 = (int)(STAGE / 32);                      // float4 groups in one plane
     long long c = 0;
     bool ok = true;
-    for (int bi = 0; bi < nblk && ok; ++bi) {
-      for (int kc = 0; kc < nKC; ++kc, ++c) {
+    for (int ii = it0; ii < it1 && ok; ++ii) {
+    const TC2Item I = tc2_item(g, items[ii], nrhs);
+    const int n4 = (int)(I.stage / 32);                    // float4 groups in one plane
+    for (int bi = 0; bi < I.nblk && ok; ++bi) {
+      for (int kc = 0; kc < I.nKC; ++kc, ++c) {
         const int st = (int)(c % nst);
         bool got = true;
         if (st_tid == 0) got = tc::bar_wait_or_abort(tc::smem_addr(&s_raw[st]), (uint32_t)((c / nst) & 1), abort_flag);
@@ -249,7 +281,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                      : "r"((uint32_t)!got), "r"(TC2_NSPL * 32)
                      : "memory");
         if (bad) { ok = false; break; }
-        float4* hi = reinterpret_cast<float4*>(smem_raw + (ring - raw) + (uint32_t)st * STAGE);
+        float4* hi = reinterpret_cast<float4*>(smem_raw + (ring - raw) + (uint32_t)st * SSTRIDE);
         float4* lo = hi + n4;
 #pragma unroll 4
         for (int v = st_tid; v < n4; v += TC2_NSPL * 32) {
@@ -267,14 +299,30 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         if (st_tid == 0) tc::bar_arrive(tc::smem_addr(&s_full[st]));
       }
     }
+    }
     if (!ok) atomicOr(err, ERRBIT_TIMEOUT);
   } else {
     // ------------------------------------------------------------------ epilogue warps 0-7
     const int q4 = warp & 3, par = warp >> 2;
     const int n = q4 * 32 + lane;                   // TMEM lane = operand row 2r + a
     const int r = n >> 1, a = n & 1;                // right-hand side within the group, part
-    const bool rok = r < nr;
     const uint32_t lanebase = tmem + ((uint32_t)(q4 * 32) << 16);
+    c32* xp = s_xpose[warp];
+    // operand row write: this lane's row (part a of right-hand side r), columns j = 8 cc .. + 7
+    auto put8 = [&](int cc, const float* v) {
+      float hi[8], lo[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) tc::split_tf32(v[e], hi[e], lo[e]);
+      tc::tmem_st8(lanebase + TC2_AH + (uint32_t)(8 * cc), hi);
+      tc::tmem_st8(lanebase + TC2_AL + (uint32_t)(8 * cc), lo);
+    };
+    long long gbi = 0;   // blocks of the items before this one (phase of s_dfull)
+    bool eok = true;
+    for (int ii = it0; ii < it1 && eok; ++ii) {
+    const TC2Item I = tc2_item(g, items[ii], nrhs);
+    const SubDesc& s = *I.s;
+    const int b = I.b, m = I.m, ng = I.ng, bp = I.bp, nblk = I.nblk, r0 = I.r0, nr = I.nr;
+    const bool rok = r < nr;
     const long long len = (long long)b * m;
     const c32* lc = (const c32*)g.lcoef + s.vofs * 5;   // planes: C, W, E, S, N
     const c32* cSp = lc + 3 * len;
@@ -293,18 +341,9 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
       gok[j] = rr < nr;
       gvo[j] = lvofs(s, r0 + (gok[j] ? rr : 0), nrhs);
     }
-    c32* xp = s_xpose[warp];
     // this thread's rows of every block: 4 consecutive rows i = 8 cc + 4 a + e (e = 0..3) of its
     // right-hand side r, for the 8-column chunks cc = par, par + 2, ... < ng
     const int nch = (ng - par + 1) / 2;
-    // operand row write: this lane's row (part a of right-hand side r), columns j = 8 cc .. + 7
-    auto put8 = [&](int cc, const float* v) {
-      float hi[8], lo[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) tc::split_tf32(v[e], hi[e], lo[e]);
-      tc::tmem_st8(lanebase + TC2_AH + (uint32_t)(8 * cc), hi);
-      tc::tmem_st8(lanebase + TC2_AL + (uint32_t)(8 * cc), lo);
-    };
     // block 0: y_0 = r_0
     for (int ci = 0; ci < nch; ++ci) {
       const int cc = par + 2 * ci;
@@ -358,8 +397,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
       // every thread's coefficient copies visible
       cp_async_wait_all();
       bool got = true;
-      if (tid == 0) got = tc::bar_spin_or_abort(tc::smem_addr(&s_dfull), (uint32_t)(bi & 1), abort_flag);
-      if (epi_any(!got)) break;
+      if (tid == 0) got = tc::bar_spin_or_abort(tc::smem_addr(&s_dfull), (uint32_t)((gbi + bi) & 1), abort_flag);
+      if (epi_any(!got)) { eok = false; break; }
       tc::fence_after();
       const bool more = bi + 1 < nblk;
       int npass = 0, nk = 0;
@@ -442,6 +481,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         prefetch(bi + 1);
         coef_copy(bi + 1);
       }
+    }
+    gbi += nblk;
     }
   }
   tc::fence_before();
@@ -532,6 +573,56 @@ bool tc2d_supported(const ddm_ctx* c, int nrt) {
   return c->d_gtc2 && nrt == TC2_NRT && tc2d_smem(c, &nst) > 0;
 }
 
+// Work lists of the persistent solve for ngr right-hand-side groups: every (subdomain, group) item
+// costs (2m - 1) b^2 (the factor entries it streams); items go out longest first, each to the
+// CTA with the least work so far (LPT), one CTA per SM.
+static cudaError_t tc2d_plan(ddm_ctx* c, int ngr, const ddm_ctx::TC2Plan** out) {
+  auto it = c->tc2plans.find(ngr);
+  if (it != c->tc2plans.end()) { *out = &it->second; return cudaSuccess; }
+  int nsm = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  std::vector<std::pair<double, int2>> work;
+  for (int sid = 0; sid < c->g.nsub; ++sid) {
+    const double b = c->subs[sid].ext[0], m = c->subs[sid].ext[1];
+    for (int gr = 0; gr < ngr; ++gr) work.push_back({(2 * m - 1) * b * b, make_int2(sid, gr)});
+  }
+  std::stable_sort(work.begin(), work.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+    return x.first > y.first;
+  });
+  const int nctas = (int)std::min<size_t>(work.size(), (size_t)std::max(nsm, 1));
+  std::vector<double> load(nctas, 0.0);
+  std::vector<std::vector<int2>> lists(nctas);
+  for (auto& w : work) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[k] += w.first;
+    lists[k].push_back(w.second);
+  }
+  std::vector<int> ofs(nctas + 1, 0);
+  std::vector<int2> items;
+  for (int k = 0; k < nctas; ++k) {
+    ofs[k + 1] = ofs[k] + (int)lists[k].size();
+    items.insert(items.end(), lists[k].begin(), lists[k].end());
+  }
+  ddm_ctx::TC2Plan pl;
+  pl.nctas = nctas;
+  if ((e = dev_alloc(c, (void**)&pl.d_ofs, sizeof(int) * ofs.size())) != cudaSuccess) return e;
+  if ((e = dev_alloc(c, (void**)&pl.d_items, sizeof(int2) * items.size())) != cudaSuccess) {
+    dev_free(c, pl.d_ofs);
+    return e;
+  }
+  if ((e = cudaMemcpyAsync(pl.d_ofs, ofs.data(), sizeof(int) * ofs.size(), cudaMemcpyHostToDevice, c->st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(pl.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, c->st)) !=
+          cudaSuccess) {
+    dev_free(c, pl.d_ofs);
+    dev_free(c, pl.d_items);
+    return e;
+  }
+  *out = &(c->tc2plans[ngr] = pl);
+  return cudaSuccess;
+}
+
 cudaError_t tc2d_solve(ddm_ctx* c, int nrt, const void* src, void* out, void* U, int nrhs) {
   if (nrt != TC2_NRT) return cudaErrorInvalidValue;
   int nst = 0;
@@ -539,10 +630,13 @@ cudaError_t tc2d_solve(ddm_ctx* c, int nrt, const void* src, void* out, void* U,
   if (!sm) return cudaErrorInvalidConfiguration;
   cudaError_t e = allow_dynamic_smem((const void*)k_solve2d_tc, sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((nrhs + TC2_NRT - 1) / TC2_NRT, c->g.nsub);
+  const ddm_ctx::TC2Plan* pl = nullptr;
+  if ((e = tc2d_plan(c, (nrhs + TC2_NRT - 1) / TC2_NRT, &pl)) != cudaSuccess) return e;
+  int bmax = 0;
+  for (auto& s : c->subs) bmax = std::max(bmax, s.ext[0]);
   ++c->nlaunch;
-  k_solve2d_tc<<<grid, TC2_THREADS, sm, c->st>>>(c->g, c->d_gtc2, c->d_tc2ofs, (const c32*)src, (c32*)out, nrhs,
-                                                 nst, c->d_err);
+  k_solve2d_tc<<<pl->nctas, TC2_THREADS, sm, c->st>>>(c->g, c->d_gtc2, c->d_tc2ofs, (const c32*)src, (c32*)out, nrhs,
+                                                      nst, (bmax + 7) / 8, pl->d_ofs, pl->d_items, c->d_err);
   if (U) {
     // after the backward sweep `out` holds the solution of every block: U += out in one pass
     const long long n = c->g.ltotal * nrhs;

@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 
 #include "ddm_internal.cuh"
+#include "tcgen05.cuh"
 
 namespace ddm {
 
@@ -343,12 +344,14 @@ __global__ void k_f3_gather(int b, int p0, int w, cplx<T>* W, int ldw, const int
 
 // W[i][j] += sum_q W[i][p0 + q] Tp[q][j] for the columns j outside the panel: 64 x 64 tiles,
 // 256 threads, 4 x 4 outputs each (rows ty + 16 a, columns tx + 16 c)
+// (columns j in [jlo, jhi) outside [xlo, xhi); tile columns start at jlo rounded down to 64)
 template <typename T>
-__global__ void __launch_bounds__(256) k_f3_rankw(int b, int p0, int w, cplx<T>* W, int ldw, const cplx<T>* Tp) {
+__global__ void __launch_bounds__(256) k_f3_rankw(int b, int p0, int w, cplx<T>* W, int ldw, const cplx<T>* Tp,
+                                                  int jlo, int jhi, int xlo, int xhi) {
   constexpr int PW = F3Panel<T>::W;
   __shared__ cplx<T> As[64][PW + 1];
   __shared__ cplx<T> Bs[PW][64];
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int i0 = blockIdx.y * 64, j0 = (jlo & ~63) + blockIdx.x * 64;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   for (int idx = tid; idx < 64 * PW; idx += 256) {
     const int ii = idx / PW, q = idx - ii * PW;
@@ -384,8 +387,125 @@ __global__ void __launch_bounds__(256) k_f3_rankw(int b, int p0, int w, cplx<T>*
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * c;
-      if (i < b && j < b && (j < p0 || j >= p0 + w)) W[(long long)i * ldw + j] = acc[a][c];
+      if (i < b && j >= jlo && j < jhi && (j < xlo || j >= xhi)) W[(long long)i * ldw + j] = acc[a][c];
     }
+}
+
+// The rank-16 update of k_f3_rankw (complex64) on the tensor cores, one 128 x 128 tile of W per
+// CTA (256 threads): D[j][i] = sum_q Tp[q][j] P[i][q], P = the panel's new columns W[i][p0 + q],
+// as a split-TF32 complex contraction (12 MMAs of M = 128 columns j, N = 128 rows i, K = 8 per
+// K step, two K steps) into two TMEM accumulators (real: columns 0-127, imaginary: 128-255); then
+// each thread (TMEM lane = column j of W, half of the rows) adds row by row: W[i][j] += D[j][i]
+// for the columns outside the panel (coalesced along j).  The operands are built in shared memory by the CTA's threads
+// (K-major core matrices, planes {re hi, re lo, im hi, im lo} of A = Tp^T and of B = P).
+constexpr int RW_T = 128, RW_K = 16;                   // tile, K (complex columns of the panel)
+constexpr int RW_PLANE = RW_T * RW_K;                  // floats per plane (8 KB)
+constexpr int RW_SMEM = 8 * RW_PLANE * 4 + 1024;       // A and B, 4 planes each, 1 KB alignment
+
+__global__ void __launch_bounds__(256, 1)
+    k_f3_rankw_tc(int b, int p0, int w, c32* W, int ldw, const c32* __restrict__ Tp, int xlo, int xhi, int* err) {
+  extern __shared__ unsigned char rw_raw[];
+  __shared__ __align__(8) uint64_t s_acc;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j0 = blockIdx.x * RW_T, i0 = blockIdx.y * RW_T;
+  const uint32_t base = (tc::smem_addr(rw_raw) + 1023u) & ~1023u;
+  float* A = reinterpret_cast<float*>(rw_raw + (base - tc::smem_addr(rw_raw)));   // 4 planes of Tp^T
+  float* B = A + 4 * RW_PLANE;                                                     // 4 planes of P
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&s_tmem), 256);
+  if (tid == 0) {
+    tc::bar_init(tc::smem_addr(&s_acc), 1);
+    tc::bar_init_fence();
+  }
+  // operands: row r of A = column j0 + r of Tp (K = q), row r of B = row i0 + r of the panel
+  for (int idx = tid; idx < RW_T * RW_K; idx += 256) {
+    const int r = idx / RW_K, q = idx - r * RW_K;
+    const int e = tc::kmajor_index(r, q, RW_K);
+    const int j = j0 + r, i = i0 + r;
+    const c32 t = (j < b && q < w) ? Tp[(long long)q * ldw + j] : mk<float>(0.f, 0.f);
+    const c32 pv = (i < b && q < w) ? W[(long long)i * ldw + p0 + q] : mk<float>(0.f, 0.f);
+    float h, l;
+    tc::split_tf32(t.x, h, l);  A[e] = h; A[RW_PLANE + e] = l;
+    tc::split_tf32(t.y, h, l);  A[2 * RW_PLANE + e] = h; A[3 * RW_PLANE + e] = l;
+    tc::split_tf32(pv.x, h, l); B[e] = h; B[RW_PLANE + e] = l;
+    tc::split_tf32(pv.y, h, l); B[2 * RW_PLANE + e] = h; B[3 * RW_PLANE + e] = l;
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = s_tmem;
+  if (tid == 0) {
+    constexpr uint32_t ID = tc::idesc_tf32(RW_T, RW_T, false);
+    constexpr uint32_t IDN = tc::idesc_tf32(RW_T, RW_T, true);
+    const uint32_t accR = tmem, accI = tmem + RW_T;
+    const uint32_t LBO = 128, SBO = (RW_K / 4) * 128;
+    const uint32_t a0 = base, b0 = base + 4 * RW_PLANE * 4;
+#pragma unroll
+    for (int ks = 0; ks < RW_K / 8; ++ks) {
+      const uint32_t ko = (uint32_t)ks * 2 * 128;   // two core matrices along K per step of 8
+      const uint64_t Arh = tc::sdesc(a0 + ko, LBO, SBO), Arl = tc::sdesc(a0 + RW_PLANE * 4 + ko, LBO, SBO);
+      const uint64_t Aih = tc::sdesc(a0 + 2 * RW_PLANE * 4 + ko, LBO, SBO), Ail = tc::sdesc(a0 + 3 * RW_PLANE * 4 + ko, LBO, SBO);
+      const uint64_t Brh = tc::sdesc(b0 + ko, LBO, SBO), Brl = tc::sdesc(b0 + RW_PLANE * 4 + ko, LBO, SBO);
+      const uint64_t Bih = tc::sdesc(b0 + 2 * RW_PLANE * 4 + ko, LBO, SBO), Bil = tc::sdesc(b0 + 3 * RW_PLANE * 4 + ko, LBO, SBO);
+      const uint32_t first = ks > 0 ? 1u : 0u;
+      // Re: Tr Pr - Ti Pi
+      tc::mma_tf32(accR, Arh, Brh, ID, first);
+      tc::mma_tf32(accR, Arh, Brl, ID, 1u);
+      tc::mma_tf32(accR, Arl, Brh, ID, 1u);
+      tc::mma_tf32(accR, Aih, Bih, IDN, 1u);
+      tc::mma_tf32(accR, Aih, Bil, IDN, 1u);
+      tc::mma_tf32(accR, Ail, Bih, IDN, 1u);
+      // Im: Tr Pi + Ti Pr
+      tc::mma_tf32(accI, Arh, Bih, ID, first);
+      tc::mma_tf32(accI, Arh, Bil, ID, 1u);
+      tc::mma_tf32(accI, Arl, Bih, ID, 1u);
+      tc::mma_tf32(accI, Aih, Brh, ID, 1u);
+      tc::mma_tf32(accI, Aih, Brl, ID, 1u);
+      tc::mma_tf32(accI, Ail, Brh, ID, 1u);
+    }
+    tc::mma_commit(tc::smem_addr(&s_acc));
+  }
+  __syncwarp();
+  const bool got = tc::bar_wait(tc::smem_addr(&s_acc), 0u);
+  const int bad = __syncthreads_or(!got);
+  tc::fence_after();
+  if (!bad) {
+    // warps q4 and q4 + 4 share TMEM lane quarter q4 (columns j) and split the rows i in halves;
+    // each thread holds the next 16 values of W in flight while it adds and stores the current 16
+    const int q4 = warp & 3, half = warp >> 2;
+    const int j = j0 + q4 * 32 + lane;
+    const bool jok = j < b && (j < xlo || j >= xhi);
+    const uint32_t lanebase = tmem + ((uint32_t)(q4 * 32) << 16);
+    const int ib = i0 + half * (RW_T / 2);
+    c32 o[16], on[16];
+    auto fetch = [&](int c0, c32* dst) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int i = ib + c0 + e;
+        dst[e] = (jok && i < b) ? W[(long long)i * ldw + j] : mk<float>(0.f, 0.f);
+      }
+    };
+    fetch(0, on);
+    for (int c0 = 0; c0 < RW_T / 2; c0 += 16) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) o[e] = on[e];
+      if (c0 + 16 < RW_T / 2) fetch(c0 + 16, on);
+      float vr[16], vi[16];
+      tc::tmem_ld16(lanebase + (uint32_t)(half * (RW_T / 2) + c0), vr);
+      tc::tmem_ld16(lanebase + (uint32_t)(RW_T + half * (RW_T / 2) + c0), vi);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int i = ib + c0 + e;
+        if (jok && i < b) W[(long long)i * ldw + j] = mk<float>(o[e].x + vr[e], o[e].y + vi[e]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, ERRBIT_TIMEOUT);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 256);
 }
 
 // G_k (column-major, ld ldb) from W with the column interchanges undone
@@ -444,6 +564,27 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   // blocked when every plane block fits the cluster panel (b <= 2048); wider planes one pivot at
   // a time
   const bool blocked = bmax <= F3C_N * F3C_T;
+  // the rank-16 updates of the blocked path on the tensor cores (complex64, blocks of at least 512
+  // rows: narrower ones keep the CUDA-core tiles, which spread over more CTAs)
+  bool rw_tc = std::is_same<T, float>::value && c->use_tc && blocked && bmax >= 512;
+  if (rw_tc && (e = allow_dynamic_smem((const void*)k_f3_rankw_tc, RW_SMEM)) != cudaSuccess) return e;
+  // the second stream and its events of the look-ahead, released on every return path
+  struct Side {
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Side() {
+      if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } side;
+  if (blocked) {
+    if ((e = cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&side.a, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&side.b, cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  cudaStream_t s2 = side.s;
+  cudaEvent_t evA = side.a, evB = side.b;
   cplx<T>* G = (cplx<T>*)c->d_G;
   for (size_t f = 0; f < reps.size(); ++f) {
     const int b = c->fac_b[f], m = c->fac_m[f], ldb = c->fac_ldb[f];
@@ -452,14 +593,37 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
       ++c->nlaunch;
       k_f3_schur<T><<<1216, 256, 0, c->st>>>(c->g, reps[f], G, fofs, ldb, k, W, ldw, cm);
       if (blocked) {
+        // look-ahead: on the context's stream the interchanges of panel p (gather), the update of
+        // panel p + 1's columns alone and the elimination of panel p + 1; on the second stream the
+        // update of every other column by panel p, beside them (disjoint columns of W).  The next
+        // gather waits for that update (it moves rows in all columns and rewrites Tp).
         const dim3 gr((b + 63) / 64, (b + 63) / 64);
+        ++c->nlaunch;
+        k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, 0, std::min(PW, b), W, ldw, perm, swl, c->d_err);
         for (int p0 = 0; p0 < b; p0 += PW) {
           const int w = std::min(PW, b - p0);
-          c->nlaunch += 3;
-          k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p0, w, W, ldw, perm, swl, c->d_err);
+          const int p1 = p0 + w, w1 = p1 < b ? std::min(PW, b - p1) : 0;
+          if (p0 > 0 && (e = cudaStreamWaitEvent(c->st, evB, 0)) != cudaSuccess) break;
+          c->nlaunch += 2;
           k_f3_gather<T><<<(b + 127) / 128, 128, 0, c->st>>>(b, p0, w, W, ldw, swl, Tp);
-          k_f3_rankw<T><<<gr, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp);
+          if ((e = cudaEventRecord(evA, c->st)) != cudaSuccess) break;
+          if (w1 > 0) {
+            const int ntx = ((p1 + w1 - 1) >> 6) - (p1 >> 6) + 1;
+            c->nlaunch += 2;
+            k_f3_rankw<T><<<dim3(ntx, (b + 63) / 64), 256, 0, c->st>>>(b, p0, w, W, ldw, Tp, p1, p1 + w1, 0, 0);
+            k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p1, w1, W, ldw, perm, swl, c->d_err);
+          }
+          if ((e = cudaStreamWaitEvent(s2, evA, 0)) != cudaSuccess) break;
+          if (rw_tc) {
+            k_f3_rankw_tc<<<dim3((b + RW_T - 1) / RW_T, (b + RW_T - 1) / RW_T), 256, RW_SMEM, s2>>>(
+                b, p0, w, (c32*)W, ldw, (const c32*)Tp, p0, p1 + w1, c->d_err);
+          } else {
+            k_f3_rankw<T><<<gr, 256, 0, s2>>>(b, p0, w, W, ldw, Tp, 0, b, p0, p1 + w1);
+          }
+          if ((e = cudaEventRecord(evB, s2)) != cudaSuccess) break;
         }
+        if (e != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(c->st, evB, 0)) != cudaSuccess) break;
       } else {
         // planes too wide for the cluster panel: one pivot at a time
         for (int p = 0; p < b; ++p) {
@@ -474,6 +638,7 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
       k_f3_store<T><<<1216, 256, 0, c->st>>>(b, W, ldw, cm, G, fofs + (long long)k * b * ldb, ldb);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
     }
+    if (e != cudaSuccess) break;
   }
   cudaStreamSynchronize(c->st);
   return e == cudaSuccess ? cudaGetLastError() : e;

@@ -290,14 +290,14 @@ __global__ void __launch_bounds__(FAC_THREADS, sizeof(T) == 4 ? 2 : 1) k_factor2
 // per panel bounds the kernel.  At the end of a line the strips go to shared memory.  The
 // permuted inverse is then written to global memory (column-major, as k_factor2d) and read back
 // for the next line's Schur complement.
-template <int RL, int NW = 4 * RL>
+template <int RL, int NW = 4 * RL, int CW = 8>
 struct FacRG {
   static constexpr int ROWS = 32 * RL;        // rows held
   static constexpr int LDC = ROWS + 2;        // row stride of the shared mirror (== 2 mod 16)
-  static constexpr int NWARP = NW;            // column strips of 8: b <= 8 NW
+  static constexpr int NWARP = NW;            // column strips of CW: b <= CW NW
   static constexpr int THREADS = 32 * NWARP;
   static size_t smem() {
-    return sizeof(c32) * ((size_t)ROWS * LDC + 2 * 8 * ROWS + 6 * ROWS) + 2 * sizeof(int) * ROWS;
+    return sizeof(c32) * ((size_t)ROWS * LDC + 2 * CW * ROWS + 6 * ROWS) + 2 * sizeof(int) * ROWS;
   }
 };
 
@@ -305,15 +305,15 @@ struct FacRG {
 // excluded from the pivot search; writes the panel's new columns to X (column-major, ROWS per
 // column) and its pivot rows to piv[8 pe + q].  W = 8 for a full panel (the loop is one block of
 // straight-line code: no branch between the pivot steps); W = 0 takes the width from b.
-template <int RL, int W>
-__device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][8], unsigned pm, const int pe, const int b, const int lane,
+template <int RL, int CW, int W>
+__device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][CW], unsigned pm, const int pe, const int b, const int lane,
                                              c32* X, int* piv, int* s_bad) {
   constexpr int ROWS = FacRG<RL>::ROWS;
-  const int w = W ? W : min(8, b - 8 * pe);
+  const int w = W ? W : min(CW, b - CW * pe);
   bool bad = false;
   int rsel = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < CW; ++q) {
     if (!W && q >= w) break;
     // pivot: the unpivoted row of largest |M[r][c]|^2 (ties to the lowest row)
     unsigned key = 0u;
@@ -326,10 +326,10 @@ __device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][8], unsigned pm, const
     key = __reduce_max_sync(0xffffffffu, key);
     const int r = key ? 255 - (int)(key & 0xFFu) : 0;
     const int tr = r >> 5, lr = r & 31;
-    c32 sv[8];
+    c32 sv[CW];
 #pragma unroll
-    for (int jo = 0; jo < 8; ++jo) {
-      const int jj = (q + jo) & 7;
+    for (int jo = 0; jo < CW; ++jo) {
+      const int jj = (q + jo) & (CW - 1);
       c32 v = R[0][jj];
 #pragma unroll
       for (int t = 1; t < RL; ++t) v = tr == t ? R[t][jj] : v;
@@ -342,13 +342,13 @@ __device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][8], unsigned pm, const
     const float rd = ok ? __frcp_rn(pa) : 0.f;
     const c32 inv = mk<float>(sv[q].x * rd, -sv[q].y * rd);
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) sv[jj] = jj == q ? inv : sv[jj] * inv;
+    for (int jj = 0; jj < CW; ++jj) sv[jj] = jj == q ? inv : sv[jj] * inv;
     c32 nf[RL];
 #pragma unroll
     for (int t = 0; t < RL; ++t) nf[t] = lane + 32 * t == r ? mk<float>(1.f, 0.f) : -R[t][q];
 #pragma unroll
-    for (int jo = 1; jo <= 8; ++jo) {
-      const int jj = (q + jo) & 7;
+    for (int jo = 1; jo <= CW; ++jo) {
+      const int jj = (q + jo) & (CW - 1);
 #pragma unroll
       for (int t = 0; t < RL; ++t) {
         const bool isr = lane + 32 * t == r;
@@ -360,30 +360,30 @@ __device__ __forceinline__ void rg_eliminate(c32 (&R)[RL][8], unsigned pm, const
     pm |= lane == lr ? 1u << tr : 0u;
     rsel = lane == q ? r : rsel;
   }
-  if (lane < w) piv[8 * pe + lane] = rsel;
+  if (lane < w) piv[CW * pe + lane] = rsel;
   if (bad && lane == 0) *s_bad = 1;
 #pragma unroll
   for (int t = 0; t < RL; ++t)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) X[q * ROWS + lane + 32 * t] = R[t][q];
+    for (int q = 0; q < CW; ++q) X[q * ROWS + lane + 32 * t] = R[t][q];
 }
 
-template <int RL>
-__device__ __forceinline__ void rg_eliminate_any(c32 (&R)[RL][8], unsigned pm, const int pe, const int b,
+template <int RL, int CW>
+__device__ __forceinline__ void rg_eliminate_any(c32 (&R)[RL][CW], unsigned pm, const int pe, const int b,
                                                  const int lane, c32* X, int* piv, int* s_bad) {
-  if (8 * pe + 8 <= b) rg_eliminate<RL, 8>(R, pm, pe, b, lane, X, piv, s_bad);
-  else rg_eliminate<RL, 0>(R, pm, pe, b, lane, X, piv, s_bad);
+  if (CW * pe + CW <= b) rg_eliminate<RL, CW, CW>(R, pm, pe, b, lane, X, piv, s_bad);
+  else rg_eliminate<RL, CW, 0>(R, pm, pe, b, lane, X, piv, s_bad);
 }
 
-template <int RL, int NW>
-__global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
+template <int RL, int NW, int CW>
+__global__ void __launch_bounds__(FacRG<RL, NW, CW>::THREADS, RL == 3 ? 2 : 1)
     k_factor2d_rg(Geom g, const int* fsel, int fsel_ofs, const int* reps, const long long* fofs_arr, const int* ldbs,
                   c32* Gout, int* err) {
-  constexpr int ROWS = FacRG<RL, NW>::ROWS, LDC = FacRG<RL, NW>::LDC;
+  constexpr int ROWS = FacRG<RL, NW, CW>::ROWS, LDC = FacRG<RL, NW, CW>::LDC;
   extern __shared__ __align__(16) unsigned char smem[];
   c32* Mst = (c32*)smem;                 // ROWS x LDC mirror of the strips (row-major)
-  c32* Xb = Mst + ROWS * LDC;            // 2 x (8 columns x ROWS): published panel columns
-  c32* cC = Xb + 2 * 8 * ROWS;           // centre of line k
+  c32* Xb = Mst + ROWS * LDC;            // 2 x (CW columns x ROWS): published panel columns
+  c32* cC = Xb + 2 * CW * ROWS;          // centre of line k
   c32* cE = cC + ROWS;                   // x+ coupling
   c32* cW = cE + ROWS;                   // x- coupling
   c32* cS = cW + ROWS;                   // coupling of line k to line k-1
@@ -398,11 +398,11 @@ __global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
   const int ldb = ldbs[f];
   const int b = sd.ext[0], m = sd.ext[1];
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int npan = (b + 7) >> 3;
-  const int col0 = 8 * warp;
+  const int npan = (b + CW - 1) / CW;
+  const int col0 = CW * warp;
   const bool has_cols = col0 < b;
   if (tid == 0) s_bad = 0;
-  c32 R[RL][8];
+  c32 R[RL][CW];
   for (int k = 0; k <= m; ++k) {
     if (k < m) {
       const long long len = (long long)b * m;
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
     for (int t = 0; t < RL; ++t) {
       const int i = lane + 32 * t;
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
+      for (int jj = 0; jj < CW; ++jj) {
         const int j = col0 + jj;
         c32 d = mk<float>(0.f, 0.f);
         if (i < b && j < b) {
@@ -447,18 +447,18 @@ __global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
     unsigned pmask = 0u;
     __syncthreads();   // everyone has read line k-1's mirror, pivots and couplings
     for (int i = tid; i < ROWS; i += nth) cNp[i] = cNn[i];
-    if (warp == 0) rg_eliminate_any<RL>(R, 0u, 0, b, lane, Xb, piv, &s_bad);
+    if (warp == 0) rg_eliminate_any<RL, CW>(R, 0u, 0, b, lane, Xb, piv, &s_bad);
     __syncthreads();
     for (int P = 0; P < npan; ++P) {
-      const int w = min(8, b - 8 * P);
-      const c32* X = Xb + (P & 1) * 8 * ROWS;
+      const int w = min(CW, b - CW * P);
+      const c32* X = Xb + (P & 1) * CW * ROWS;
       // the panel's pivot rows leave the search
-      int rq[8];
+      int rq[CW];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) rq[q] = q < w ? piv[8 * P + q] : piv[8 * P];
+      for (int q = 0; q < CW; ++q) rq[q] = q < w ? piv[CW * P + q] : piv[CW * P];
       const unsigned before = pmask;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) pmask |= (q < w && (rq[q] & 31) == lane) ? 1u << (rq[q] >> 5) : 0u;
+      for (int q = 0; q < CW; ++q) pmask |= (q < w && (rq[q] & 31) == lane) ? 1u << (rq[q] >> 5) : 0u;
       const unsigned fresh = pmask & ~before;
       // the owner of the next panel updates its strip first, then signals (named barrier 1) and
       // eliminates; the other warps update theirs after the signal, beside the elimination
@@ -472,20 +472,20 @@ __global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
         for (int t = 0; t < RL; ++t) {
           float4* dst = (float4*)(my + (lane + 32 * t) * LDC);
 #pragma unroll
-          for (int h = 0; h < 4; ++h) dst[h] = make_float4(R[t][2 * h].x, R[t][2 * h].y, R[t][2 * h + 1].x, R[t][2 * h + 1].y);
+          for (int h = 0; h < CW / 2; ++h) dst[h] = make_float4(R[t][2 * h].x, R[t][2 * h].y, R[t][2 * h + 1].x, R[t][2 * h + 1].y);
         }
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < RL; ++t)
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) R[t][jj] = ((fresh >> t) & 1u) ? mk<float>(0.f, 0.f) : R[t][jj];
+          for (int jj = 0; jj < CW; ++jj) R[t][jj] = ((fresh >> t) & 1u) ? mk<float>(0.f, 0.f) : R[t][jj];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < CW; ++q) {
           // q >= w (a partial last panel): X[q] is zero there, the product adds nothing
           const float4* src = (const float4*)(my + rq[q] * LDC);
-          c32 T[8];
+          c32 T[CW];
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
+          for (int h = 0; h < CW / 2; ++h) {
             const float4 v = src[h];
             T[2 * h] = mk<float>(v.x, v.y);
             T[2 * h + 1] = mk<float>(v.z, v.w);
@@ -494,14 +494,14 @@ __global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
           for (int t = 0; t < RL; ++t) {
             const c32 xv = X[q * ROWS + lane + 32 * t];
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) cfma(R[t][jj], xv, T[jj]);
+            for (int jj = 0; jj < CW; ++jj) cfma(R[t][jj], xv, T[jj]);
           }
         }
         __syncwarp();
       }
       if (owner_next) {
         asm volatile("bar.arrive 1, %0;" ::"r"(nth) : "memory");
-        rg_eliminate_any<RL>(R, pmask, P + 1, b, lane, Xb + ((P + 1) & 1) * 8 * ROWS, piv, &s_bad);
+        rg_eliminate_any<RL, CW>(R, pmask, P + 1, b, lane, Xb + ((P + 1) & 1) * CW * ROWS, piv, &s_bad);
       }
       __syncthreads();
     }
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(FacRG<RL, NW>::THREADS, RL == 3 ? 2 : 1)
       for (int t = 0; t < RL; ++t) {
         float4* dst = (float4*)(my + (lane + 32 * t) * LDC);
 #pragma unroll
-        for (int h = 0; h < 4; ++h) dst[h] = make_float4(R[t][2 * h].x, R[t][2 * h].y, R[t][2 * h + 1].x, R[t][2 * h + 1].y);
+        for (int h = 0; h < CW / 2; ++h) dst[h] = make_float4(R[t][2 * h].x, R[t][2 * h].y, R[t][2 * h + 1].x, R[t][2 * h + 1].y);
       }
     }
     for (int c = tid; c < b; c += nth) rinv[piv[c]] = c;
@@ -530,14 +530,15 @@ size_t factor_smem_bytes(int b, int ldb, int prec) {
 // d_ldb[f] its storage offset and leading dimension.  complex64: the register-resident kernel,
 // one launch per block-width class (b <= 96: 12 warps, two CTAs per SM; b <= 128: 16 warps);
 // complex128: k_factor2d.
-template <int RL, int NW>
+template <int RL, int NW, int CW>
 static cudaError_t launch_rg(ddm_ctx* c, int n, int ofs, const int* d_reps, const long long* d_fofs, const int* d_ldb) {
   if (n <= 0) return cudaSuccess;
-  cudaError_t e = allow_dynamic_smem((const void*)k_factor2d_rg<RL, NW>, FacRG<RL, NW>::smem());
+  using F = FacRG<RL, NW, CW>;
+  cudaError_t e = allow_dynamic_smem((const void*)k_factor2d_rg<RL, NW, CW>, F::smem());
   if (e != cudaSuccess) return e;
   ++c->nlaunch;
-  k_factor2d_rg<RL, NW><<<n, FacRG<RL, NW>::THREADS, FacRG<RL, NW>::smem(), c->st>>>(
-      c->g, c->d_fsel, ofs, d_reps, d_fofs, d_ldb, (c32*)c->d_G, c->d_err);
+  k_factor2d_rg<RL, NW, CW><<<n, F::THREADS, F::smem(), c->st>>>(c->g, c->d_fsel, ofs, d_reps, d_fofs, d_ldb,
+                                                                   (c32*)c->d_G, c->d_err);
   return cudaGetLastError();
 }
 
@@ -553,8 +554,8 @@ cudaError_t launch_factor_all(ddm_ctx* c, const int* d_reps, const long long* d_
     if ((e = cudaMemcpyAsync(c->d_fsel, sel.data(), sizeof(int) * sel.size(), cudaMemcpyHostToDevice, c->st)) !=
         cudaSuccess)
       return e;
-    if ((e = launch_rg<3, 12>(c, cnt[0], 0, d_reps, d_fofs, d_ldb)) != cudaSuccess) return e;
-    return launch_rg<4, 16>(c, cnt[1], cnt[0], d_reps, d_fofs, d_ldb);
+    if ((e = launch_rg<3, 12, 8>(c, cnt[0], 0, d_reps, d_fofs, d_ldb)) != cudaSuccess) return e;
+    return launch_rg<4, 16, 8>(c, cnt[1], cnt[0], d_reps, d_fofs, d_ldb);
   }
   size_t sm = 0;
   for (int f = 0; f < c->nfac; ++f) sm = std::max(sm, factor_smem_bytes(c->fac_b[f], c->fac_ldb[f], c->prec));

@@ -3,9 +3,11 @@
 Default workload: 2D heterogeneous medium, 1024^2 interior (1048^2 with the 12-cell overlap +
 PML band), c in [1.5, 4.5] as a seeded sum of 20 Gaussians, 10 points per wavelength at
 c_min, 16x16 subdomains, one single-shot source, complex64 local factors/solves inside FP64
-FGMRES(60) preconditioned by K = 16 DDM steps (the fastest K measured on this workload; the
-number of local solves to 1e-6 is nearly independent of K, as in the paper's Table 5, while
-the FP64 Arnoldi work falls with the iteration count), tolerance 1e-6.
+FGMRES(60) preconditioned by K = 40 DDM steps, tolerance 1e-6.  K is the method's free
+parameter (the paper's Tables 5-6 vary it); 40 was the fastest in a sweep on this workload:
+FGMRES then needs two iterations, 80 local solves, where K = 16 needs six iterations and 96
+local solves.  Each preconditioner application is replayed as a CUDA graph (--no-graph turns
+that off).
 
 One step = the whole hot path for one problem instance: assemble the medium (k^2), factor
 all 256 subdomain operators, and solve to a relative residual of 1e-6 (FGMRES, DDM steps,
@@ -125,6 +127,8 @@ def run_ours(args, rank, world, local_rank):
     mode = D.DDM_FGMRES if args.mode == "fgmres" else D.DDM_STEPPING
     s = D.Solver(wl, precision=prec, max_rhs=1, device=str(dev))
     ctx = s.ctx
+    if args.graph:
+        D.ddm_set_graph(ctx, True)
     c_dev = s.c
     f_dev = s.to_dev(wl.f[0])
     u_dev = torch.zeros(wl.c.shape, dtype=torch.complex128, device=dev)
@@ -175,12 +179,18 @@ def run_ours(args, rank, world, local_rank):
     # the kernel split and the local solve's launch time come from a separate pass of the same
     # steps with the library's per-launch CUDA events on (recorded on the library's stream), so
     # that the timed region above carries no instrumentation
+    # (with graph replay on, the instrumented steps launch the same kernels one by one, so that the
+    # split and the local solve's launch time are per kernel)
     n_prof = max(1, min(args.steps, 5))
+    if args.graph:
+        D.ddm_set_graph(ctx, False)
     D.ddm_timing(ctx, enable=True, reset=True)
     for _ in range(n_prof):
         step()
     torch.cuda.synchronize()
     tms = D.ddm_timing(ctx, enable=False)
+    if args.graph:
+        D.ddm_set_graph(ctx, True)
     # dominant kernel: the batched local solves (k_solve2d)
     solve_ms, solve_n = tms["solve"]
     per_solve_bytes, stored = D.ddm_factor_bytes(ctx)
@@ -189,6 +199,19 @@ def run_ours(args, rank, world, local_rank):
     vec_bytes = 6 * lay["total"] * el          # src read, t write/read, x write, U read+write
     launch_bytes = per_solve_bytes + vec_bytes
     avg_launch_ms = solve_ms / max(solve_n, 1)
+    if solve_n == 0:
+        # graph replay: the local solves are timed inside the replayed graphs, so time one launch
+        # of the same local solve directly on the library's stream
+        src = torch.randn(lay["total"], dtype=torch.complex64 if prec == D.DDM_MIXED else torch.complex128, device=dev)
+        dst = torch.zeros_like(src)
+        D.ddm_local_solve(ctx, src, dst, 1)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(10):
+            D.ddm_local_solve(ctx, src, dst, 1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        avg_launch_ms, solve_n = ev0.elapsed_time(ev1) / 10, 10
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9
     pk = peaks()
     traffic = solve_traffic(args.precision)
@@ -201,7 +224,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl.name + " (2D heterogeneous, c in [1.5,4.5] sum of 20 seeded Gaussians, "
                    "10 ppw at c_min, single-shot source)",
                    "grid": "1024^2 interior + 12-cell overlap/PML band (1048^2)", "subdomains": "16x16 of 64^2 (+2 ov +10 pml)",
-                   "precision": args.precision, "mode": args.mode, "K": args.K, "restart": args.restart,
+                   "precision": args.precision, "mode": args.mode, "K": args.K, "restart": args.restart, "graph": args.graph,
                    "tol": wl.tol, "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 ({stored / 1e9:.2f} GB of factors streamed per sweep)"},
         "time_to_solution_ms": info_last.get("solve_ms"), "factor_ms": info_last.get("factor_ms"),
@@ -213,7 +236,8 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": traffic, "algorithmic_bytes_per_launch": launch_bytes,
                      "avg_launch_ms": avg_launch_ms, "launches": solve_n},
         "kernel_ms": {k: v[0] / n_prof for k, v in tms.items()},
-        "kernel_ms_note": f"per step, from {n_prof} instrumented steps after the timed region",
+        "kernel_ms_note": f"per step, from {n_prof} instrumented steps after the timed region (kernels launched "
+                          f"one by one)",
         "gpu_launches": launches, "clocks": ck,
     }
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -667,7 +691,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--mode", choices=["fgmres", "stepping"], default="fgmres")
-    ap.add_argument("--K", type=int, default=16)
+    ap.add_argument("--K", type=int, default=40)
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="launch the preconditioner's kernels one by one instead of replaying a CUDA graph")
     ap.add_argument("--restart", type=int, default=60)
     ap.add_argument("--max-it", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")

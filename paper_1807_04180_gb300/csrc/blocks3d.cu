@@ -518,11 +518,32 @@ __global__ void k_f3_store(int b, const cplx<T>* W, int ldw, const int* cm, cplx
   }
 }
 
+// the column map undoing the interchanges: the swaps are sequential, so one thread applies them in
+// shared memory (the maps loaded and stored by the whole CTA); dynamic shared memory 2 b ints
 __global__ void k_f3_colmap(int b, const int* perm, int* cm) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    for (int j = 0; j < b; ++j) cm[j] = j;
-    for (int p = b - 1; p >= 0; --p) { const int q = perm[p]; const int t = cm[p]; cm[p] = cm[q]; cm[q] = t; }
-  }
+  extern __shared__ int cm_sh[];
+  int* sp = cm_sh;
+  int* sc = cm_sh + b;
+  for (int j = threadIdx.x; j < b; j += blockDim.x) { sp[j] = perm[j]; sc[j] = j; }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int p = b - 1; p >= 0; --p) { const int q = sp[p]; const int t = sc[p]; sc[p] = sc[q]; sc[q] = t; }
+  __syncthreads();
+  for (int j = threadIdx.x; j < b; j += blockDim.x) cm[j] = sc[j];
+}
+
+// the update of the columns [c0, c0 + nc) alone by panel [p0, p0 + w) (the next panel's columns,
+// on the look-ahead's critical path): one output per thread, W[i][j] += sum_q W[i][p0 + q] Tp[q][j]
+// (the old pivot rows are zero in W, so they take their new values)
+template <typename T>
+__global__ void k_f3_rankw_cols(int b, int p0, int w, cplx<T>* W, int ldw, const cplx<T>* Tp, int c0, int nc) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int i = (int)(idx / nc), jj = (int)(idx - (long long)i * nc);
+  if (i >= b) return;
+  const int j = c0 + jj;
+  cplx<T> acc = W[(long long)i * ldw + j];
+  for (int q = 0; q < w; ++q) cfma(acc, W[(long long)i * ldw + p0 + q], Tp[(long long)q * ldw + j]);
+  W[(long long)i * ldw + j] = acc;
 }
 
 template <typename T>
@@ -568,6 +589,7 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   // rows: narrower ones keep the CUDA-core tiles, which spread over more CTAs)
   bool rw_tc = std::is_same<T, float>::value && c->use_tc && blocked && bmax >= 512;
   if (rw_tc && (e = allow_dynamic_smem((const void*)k_f3_rankw_tc, RW_SMEM)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem((const void*)k_f3_colmap, 2 * sizeof(int) * (size_t)bmax)) != cudaSuccess) return e;
   // the second stream and its events of the look-ahead, released on every return path
   struct Side {
     cudaStream_t s = nullptr;
@@ -608,9 +630,8 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
           k_f3_gather<T><<<(b + 127) / 128, 128, 0, c->st>>>(b, p0, w, W, ldw, swl, Tp);
           if ((e = cudaEventRecord(evA, c->st)) != cudaSuccess) break;
           if (w1 > 0) {
-            const int ntx = ((p1 + w1 - 1) >> 6) - (p1 >> 6) + 1;
             c->nlaunch += 2;
-            k_f3_rankw<T><<<dim3(ntx, (b + 63) / 64), 256, 0, c->st>>>(b, p0, w, W, ldw, Tp, p1, p1 + w1, 0, 0);
+            k_f3_rankw_cols<T><<<(b * w1 + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp, p1, w1);
             k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p1, w1, W, ldw, perm, swl, c->d_err);
           }
           if ((e = cudaStreamWaitEvent(s2, evA, 0)) != cudaSuccess) break;
@@ -634,7 +655,7 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
         }
       }
       c->nlaunch += 2;
-      k_f3_colmap<<<1, 1, 0, c->st>>>(b, perm, cm);
+      k_f3_colmap<<<1, 256, 2 * sizeof(int) * b, c->st>>>(b, perm, cm);
       k_f3_store<T><<<1216, 256, 0, c->st>>>(b, W, ldw, cm, G, fofs + (long long)k * b * ldb, ldb);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
     }

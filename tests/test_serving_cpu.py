@@ -66,6 +66,7 @@ class Harness:
         srv.precision = D.DDM_MIXED
         srv.K, srv.restart, srv.max_it = 16, 20, 10
         srv.keep_results = True
+        srv.collect_timing = False
         srv.policy = policy
         srv._rate = 3e-8
         srv._cv = threading.Condition()

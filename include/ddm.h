@@ -191,6 +191,58 @@ ddm_status ddm_set_tensor_cores(ddm_ctx *ctx, int enable);
  * met).                                                                     */
 ddm_status ddm_set_rhs_per_cta(ddm_ctx *ctx, int nr);
 
+/* Local solver of Algorithm 3.1's subdomain problems.  The paper factors
+ * each subdomain with a sparse direct (multifrontal) solver (Section 4).
+ * DDM_LOCAL_BLOCK (the default): the block-tridiagonal LU in explicit-inverse
+ * form described at ddm_factor.  DDM_LOCAL_ND (2D partitions only): a
+ * multifrontal factorisation in nested-dissection order.  Each subdomain grid
+ * is bisected recursively by grid lines until boxes of at most `leaf` nodes
+ * remain (leaf 0: DDM_ND_LEAF_DEFAULT).  Every tree node's front is swept by
+ * Gauss-Jordan over its separator, with partial pivoting inside the
+ * separator.  A solve is one forward and one backward pass over the tree
+ * heights, all subdomains and right-hand sides in the same launches.  At the
+ * paper's 300^2 + PML subdomains it stores about 1/6 of the block factor's
+ * entries and needs about 1/14 of its flops.  Its fronts, blocks and
+ * arithmetic are FP64 in both precisions (CUDA cores): an interior front is
+ * a box problem without PML damping, and near a resonance its pivot block is
+ * too ill-conditioned for complex64.  In DDM_MIXED contexts only the source,
+ * the output and U are complex64.  A change takes effect
+ * at the next ddm_factor: the context is unfactored until then.  It also
+ * drops captured graphs.  ddm_workspace_bytes bounds the default solver only.
+ * Errors: DDM_E_INVAL (unknown solver, leaf outside 0..4096, DDM_LOCAL_ND on
+ * a 3D partition, or DDM_LOCAL_BLOCK with graph replay on where the block
+ * solver cannot replay).                                                    */
+enum { DDM_LOCAL_BLOCK = 0, DDM_LOCAL_ND = 1 };
+#define DDM_ND_LEAF_DEFAULT 32
+ddm_status ddm_set_local_solver(ddm_ctx *ctx, int solver, int leaf);
+
+/* The nested-dissection plan of an nx x ny subdomain grid (x fastest, node
+ * index y*nx + x) with leaves of at most `leaf` nodes (0: the default).  Pure
+ * host computation, no CUDA call.  Fills *info; each array that is not NULL
+ * receives, with indices local to the plan:
+ *   fronts  nfront x 12 ints, children before parents, the root last:
+ *           s (pivots), d (boundary nodes), height (leaves 0), offset of its
+ *           pivots in piv, offset of its boundary nodes in bnd, child 0,
+ *           child 1 (-1 if none), offsets in cmap of child 0's and child 1's
+ *           boundary positions, offset and count of its entries in ent,
+ *           offset of its update vector;
+ *   piv     n_piv node indices, the pivots of every front in elimination order;
+ *   bnd     n_bnd node indices, each front's boundary nodes in ascending order;
+ *   cmap    n_cmap positions (0..s+d-1) in the parent front of each child
+ *           boundary node;
+ *   ent     n_ent x 4 ints (row, col, node, plane): front[row][col] gets the
+ *           operator's plane `plane` (0 centre, 1 x-, 2 x+, 3 y-, 4 y+) at
+ *           local node `node`.
+ * The factor stores factor_entries = sum over fronts of (s+d)*s elements.
+ * Errors: DDM_E_INVAL (NULL info, nx or ny outside 1..4096, bad leaf).       */
+typedef struct {
+  int nfront, height;
+  int64_t n_piv, n_bnd, n_cmap, n_ent;
+  int64_t factor_entries, scratch_entries, update_entries;
+} ddm_nd_plan_info;
+ddm_status ddm_nd_plan(int nx, int ny, int leaf, ddm_nd_plan_info *info, int *fronts, int *piv, int *bnd, int *cmap,
+                       int *ent);
+
 /* Upper bound of the device bytes a context for `p` holds after ddm_setup,
  * ddm_factor (every subdomain counted with its own factor) and an FGMRES
  * solve of p->max_rhs right-hand sides with the given restart (0: no FGMRES

@@ -18,7 +18,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["api.cu", "setup.cu", "factor.cu", "solve.cu", "transfer.cu", "krylov.cu", "noalloc.cu", "blocks3d.cu", "tc3d.cu", "tc2d.cu"]
+SOURCES = ["api.cu", "setup.cu", "factor.cu", "solve.cu", "transfer.cu", "krylov.cu", "noalloc.cu", "blocks3d.cu", "tc3d.cu", "tc2d.cu", "nd.cu"]
 
 
 def nvcc() -> str:

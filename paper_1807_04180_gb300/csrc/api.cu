@@ -320,6 +320,7 @@ extern "C" ddm_status ddm_destroy(ddm_ctx* c) {
   if (!c) return DDM_OK;
   cudaStreamSynchronize(c->st);
   for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+  nd_free(c);
   if (c->gstream) cudaStreamSynchronize(c->gstream), cudaStreamDestroy(c->gstream);
   for (auto ev : c->gev) if (ev) cudaEventDestroy(ev);
   dev_free(c, c->d_gin);
@@ -423,8 +424,11 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
     c->subs[s].pad = c->fac_ldb[f];
   }
   c->nfac = (int)reps.size();
+  const bool nd = c->local_solver == DDM_LOCAL_ND;
+  if (nd) CK(nd_layout(c, reps, &ofs));   // the multifrontal blocks replace the block layout
   c->fac_elems = ofs;
-  const size_t gbytes = (size_t)ofs * local_elem(c);
+  // the nested-dissection blocks are FP64 in both precisions
+  const size_t gbytes = (size_t)ofs * (nd ? sizeof(z64) : local_elem(c));
   if (gbytes > c->G_cap) {
     dev_free(c, c->d_G);
     c->d_G = nullptr;
@@ -445,7 +449,9 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   cudaEventRecord(e0, c->st);
   {
     TScope ts(c, T_FACTOR);
-    if (!c->blockpath) {
+    if (nd) {
+      CK(nd_factor(c, reps));
+    } else if (!c->blockpath) {
       CK(launch_factor_all(c, d_reps, d_fofs, d_ldb));
       if (c->prec == DDM_MIXED && c->p.max_rhs >= 16) CK(tc2d_pack_factors(c));
     }
@@ -937,9 +943,30 @@ extern "C" ddm_status ddm_timing(ddm_ctx* c, int enable, int reset, double* out_
 
 extern "C" ddm_status ddm_set_graph(ddm_ctx* c, int enable) {
   if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
-  if (enable && c->blockpath)
-    return fail(c, DDM_E_INVAL, "graph replay of M_K is implemented for 2D partitions of subdomains at most 128 nodes wide");
+  if (enable && c->blockpath && c->local_solver != DDM_LOCAL_ND)
+    return fail(c, DDM_E_INVAL,
+                "graph replay of M_K is implemented for 2D partitions: subdomains at most 128 nodes wide, or the "
+                "nested-dissection local solver");
   c->use_graph = enable != 0;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_set_local_solver(ddm_ctx* c, int solver, int leaf) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (solver != DDM_LOCAL_BLOCK && solver != DDM_LOCAL_ND)
+    return fail(c, DDM_E_INVAL, "local solver must be DDM_LOCAL_BLOCK or DDM_LOCAL_ND");
+  if (leaf < 0 || leaf > 4096) return fail(c, DDM_E_INVAL, "leaf size must be 0 (default) .. 4096 nodes");
+  if (solver == DDM_LOCAL_ND && c->dim != 2)
+    return fail(c, DDM_E_INVAL, "the nested-dissection local solver is built for 2D partitions");
+  if (solver == DDM_LOCAL_BLOCK && c->use_graph && c->blockpath)
+    return fail(c, DDM_E_INVAL, "the block solver of these subdomains cannot replay graphs: turn the graph off first");
+  const int lf = leaf == 0 ? DDM_ND_LEAF_DEFAULT : leaf;
+  if (solver != c->local_solver || lf != c->nd_leaf) {
+    c->factored = false;
+    c->drop_graphs();
+  }
+  c->local_solver = solver;
+  c->nd_leaf = lf;
   return DDM_OK;
 }
 
@@ -1037,7 +1064,9 @@ extern "C" ddm_status ddm_factor_bytes(const ddm_ctx* c, int64_t* per_solve, int
   if (!c || !c->factored) return DDM_E_STATE;
   const long long el = (long long)local_elem(c);
   long long ps = 0;
-  if (!c->blockpath) {
+  if (c->local_solver == DDM_LOCAL_ND) {
+    ps = nd_read_elems(c) * (long long)sizeof(z64);
+  } else if (!c->blockpath) {
     for (auto& s : c->subs) {
       long long b = s.ext[0], m = s.ext[1];
       ps += (2 * m - 1) * b * b * el;
@@ -1046,7 +1075,7 @@ extern "C" ddm_status ddm_factor_bytes(const ddm_ctx* c, int64_t* per_solve, int
     for (int f = 0; f < c->nfac; ++f) ps += (2LL * c->fac_m[f] - 1) * c->fac_b[f] * (long long)c->fac_b[f] * el;
   }
   if (per_solve) *per_solve = ps;
-  if (stored) *stored = c->fac_elems * el;
+  if (stored) *stored = c->fac_elems * (c->local_solver == DDM_LOCAL_ND ? (long long)sizeof(z64) : el);
   return DDM_OK;
 }
 

@@ -145,6 +145,7 @@ __device__ __forceinline__ Coef coef_at(const Geom& g, const int* tofs, const in
 // ---------------------------------------------------------------------------
 enum { T_SOLVE = 0, T_TRANSFER, T_ASSEMBLE, T_GLOBAL, T_KRYLOV, T_FACTOR, T_GRAPH, T_NSLOT };
 
+namespace nd { struct State; }
 }  // namespace ddm
 
 // ---------------------------------------------------------------------------
@@ -264,6 +265,10 @@ struct ddm_ctx {
   long long* d_fofs = nullptr;            // nsub
   int* d_fsel = nullptr;                  // nsub: factor ids in launch order (by kernel variant)
   ddm::z64* d_coef = nullptr;             // (kry_m + 1) x kry_nb Gram-Schmidt coefficients
+  // local solver (ddm_set_local_solver) and the nested-dissection plans, work lists and buffers
+  int local_solver = DDM_LOCAL_BLOCK;
+  int nd_leaf = DDM_ND_LEAF_DEFAULT;
+  ddm::nd::State* nd = nullptr;
   std::string err;
 };
 
@@ -327,6 +332,13 @@ cudaError_t tc2d_pack_factors(ddm_ctx* c);
 bool tc2d_supported(const ddm_ctx* c, int nrt);
 cudaError_t tc2d_solve(ddm_ctx* c, int nrt, const void* src, void* out, void* U, int nrhs);
 cudaError_t tc3d_pack_factors(ddm_ctx* c);
+// nested-dissection local solver (nd.cu): factor-store layout (sets c->fac_ofs, returns the
+// total elements), factorisation of the distinct factors, batched local solve, release
+cudaError_t nd_layout(ddm_ctx* c, const std::vector<int>& reps, long long* elems);
+cudaError_t nd_factor(ddm_ctx* c, const std::vector<int>& reps);
+cudaError_t nd_solve(ddm_ctx* c, const void* src, void* out, void* U, int nrhs);
+void nd_free(ddm_ctx* c);
+long long nd_read_elems(const ddm_ctx* c);
 cudaError_t tc3d_sweeps(ddm_ctx* c, int f, const long long* d_colofs, int ncol, const c32* cS, const c32* cN,
                         const c32* src, c32* out, c32* U);
 }  // namespace ddm

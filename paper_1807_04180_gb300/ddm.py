@@ -26,6 +26,8 @@ DDM_OK, DDM_E_INVAL, DDM_E_NOMEM, DDM_E_CUDA, DDM_E_STATE, DDM_E_SINGULAR, DDM_E
     DDM_E_BUDGET = range(9)
 DDM_FP64, DDM_MIXED = 0, 1
 DDM_STEPPING, DDM_FGMRES = 0, 1
+DDM_LOCAL_BLOCK, DDM_LOCAL_ND = 0, 1
+DDM_ND_LEAF_DEFAULT = 32
 STATUS_NAMES = ["DDM_OK", "DDM_E_INVAL", "DDM_E_NOMEM", "DDM_E_CUDA", "DDM_E_STATE", "DDM_E_SINGULAR",
                 "DDM_E_NOCONV", "DDM_E_TIMEOUT", "DDM_E_BUDGET"]
 TIMING_SLOTS = ["solve", "transfer", "assemble", "global", "krylov", "factor", "graph"]
@@ -46,6 +48,13 @@ class ddm_info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ddm_nd_plan_info(ctypes.Structure):
+    _fields_ = [("nfront", ctypes.c_int), ("height", ctypes.c_int), ("n_piv", ctypes.c_int64),
+                ("n_bnd", ctypes.c_int64), ("n_cmap", ctypes.c_int64), ("n_ent", ctypes.c_int64),
+                ("factor_entries", ctypes.c_int64), ("scratch_entries", ctypes.c_int64),
+                ("update_entries", ctypes.c_int64)]
 
 
 class DDMError(RuntimeError):
@@ -94,6 +103,9 @@ def lib() -> ctypes.CDLL:
         "ddm_set_graph": [_P, ctypes.c_int],
         "ddm_set_tensor_cores": [_P, ctypes.c_int],
         "ddm_set_rhs_per_cta": [_P, ctypes.c_int],
+        "ddm_set_local_solver": [_P, ctypes.c_int, ctypes.c_int],
+        "ddm_nd_plan": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ddm_nd_plan_info), _P, _P, _P, _P,
+                        _P],
         "ddm_autotune_log": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)],
     }
@@ -185,6 +197,27 @@ def ddm_set_tensor_cores(ctx, enable: bool = True) -> None:
 
 def ddm_set_rhs_per_cta(ctx, nr: int = 0) -> None:
     _check(lib().ddm_set_rhs_per_cta(ctx, int(nr)), ctx)
+
+
+def ddm_set_local_solver(ctx, solver: int = DDM_LOCAL_BLOCK, leaf: int = 0) -> None:
+    _check(lib().ddm_set_local_solver(ctx, int(solver), int(leaf)), ctx)
+
+
+def ddm_nd_plan(nx: int, ny: int, leaf: int = 0) -> dict:
+    """Nested-dissection plan of an nx x ny grid (host only): the info fields plus the arrays
+    fronts (nfront x 12), piv, bnd, cmap and ent (n_ent x 4) as numpy int32 arrays."""
+    info = ddm_nd_plan_info()
+    L = lib()
+    _check(L.ddm_nd_plan(int(nx), int(ny), int(leaf), ctypes.byref(info), None, None, None, None, None), None)
+    arrs = {"fronts": np.zeros((max(info.nfront, 1), 12), np.int32), "piv": np.zeros(max(info.n_piv, 1), np.int32),
+            "bnd": np.zeros(max(info.n_bnd, 1), np.int32), "cmap": np.zeros(max(info.n_cmap, 1), np.int32),
+            "ent": np.zeros((max(info.n_ent, 1), 4), np.int32)}
+    _check(L.ddm_nd_plan(int(nx), int(ny), int(leaf), ctypes.byref(info),
+                         *(a.ctypes.data_as(_P) for a in arrs.values())), None)
+    out = {k: getattr(info, k) for k, _ in info._fields_}
+    out.update({"fronts": arrs["fronts"][:info.nfront], "piv": arrs["piv"][:info.n_piv],
+                "bnd": arrs["bnd"][:info.n_bnd], "cmap": arrs["cmap"][:info.n_cmap], "ent": arrs["ent"][:info.n_ent]})
+    return out
 
 
 def ddm_workspace_bytes(params: ddm_params, restart: int) -> int:
@@ -362,7 +395,8 @@ def ddm_norms_noalloc(x_dev, n: int, nvec: int, norms_dev, stream=None) -> None:
 class Solver:
     """Owns one context: set-up from a Workload, factor, apply, solve."""
 
-    def __init__(self, wl, precision: int = DDM_FP64, max_rhs: int = 1, device: str = "cuda", stream=None):
+    def __init__(self, wl, precision: int = DDM_FP64, max_rhs: int = 1, device: str = "cuda", stream=None,
+                 local_solver: int = DDM_LOCAL_BLOCK, leaf: int = 0):
         import torch
         self.wl = wl
         self.precision = precision
@@ -372,6 +406,8 @@ class Solver:
         self.stream = stream
         self.ctx = ddm_setup(self._params, wl.omega, self.c, stream)
         self.gshape = tuple(wl.c.shape)
+        if local_solver != DDM_LOCAL_BLOCK or leaf:
+            ddm_set_local_solver(self.ctx, local_solver, leaf)
 
     def factor(self):
         ddm_factor(self.ctx)

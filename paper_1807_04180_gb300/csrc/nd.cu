@@ -43,6 +43,8 @@
 #include <map>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "ddm_internal.cuh"
 
 namespace ddm {
@@ -295,6 +297,149 @@ __global__ void __launch_bounds__(FT) k_nd_factor(Geom g, const int2* __restrict
       const int a = i / d, b = i - a * d;
       Fg[(long long)(s + a) * m + s + b] = A[(s + a) * m + s + b];
     }
+}
+
+// A front too large for shared memory is swept by a cluster of NDC CTAs in place in its global
+// scratch: CTA q owns the rows i = q (mod NDC).  Per pivot: every CTA finds the best of its own
+// candidate rows and publishes it in shared memory; after a cluster barrier each CTA reads the
+// NDC candidates (distributed shared memory) and agrees on the pivot row r, copies rows r and k
+// (scaled and old) and its own rows' column k, then after a second barrier updates its own
+// rows.  Loads of the front bypass L1 (other CTAs write the lines), and the cluster barriers
+// order the global writes between CTAs.  Every thread of every CTA passes the same barriers
+// (the loop bounds are the front's sizes), so they cannot deadlock.
+constexpr int NDC = 8;
+
+__device__ __forceinline__ z64 ldcg(const z64* p) {
+  const double2 v = __ldcg((const double2*)p);
+  return mk<double>(v.x, v.y);
+}
+
+template <typename TC>
+__global__ void __cluster_dims__(NDC, 1, 1) __launch_bounds__(FT)
+    k_nd_factor_cl(Geom g, const int2* __restrict__ items, const FrontD* __restrict__ fr, const int* __restrict__ cmap,
+                   const int2* __restrict__ ent, const int* __restrict__ reps, const long long* __restrict__ ffofs,
+                   const long long* __restrict__ fscr, z64* __restrict__ G, z64* scr, int mcap, int scap, int* err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smem[];
+  typedef z64 C;
+  typedef double T;
+  __shared__ T cand_v;
+  __shared__ int cand_i;
+  const int2 it = items[blockIdx.x / NDC];
+  const int f = it.x;
+  const FrontD F = fr[it.y];
+  const int s = F.s, d = F.d, m = s + d;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FT / 32;
+  const int gt = q * FT + tid, GT = NDC * FT;
+  const SubDesc& sd = g.subs[reps[f]];
+  const long long len = (long long)sd.ext[0] * sd.ext[1];
+  const cplx<TC>* lc = (const cplx<TC>*)g.lcoef + sd.vofs * 5;
+  C* A = scr + fscr[f] + F.fofs;
+  C* rowk = (C*)smem;
+  C* rowo = rowk + mcap;
+  C* colk = rowo + mcap;                                  // own rows' column k: (mcap + NDC - 1) / NDC
+  int* perm = (int*)(colk + (mcap + NDC - 1) / NDC);
+  int* colsrc = perm + scap;
+  T* redv = (T*)(colsrc + scap);
+  int* redi = (int*)(redv + nw);
+
+  for (long long i = gt; i < (long long)m * m; i += GT) A[i] = mk<T>(0, 0);
+  cl.sync();
+  for (int e = F.ent + gt; e < F.ent + F.nent; e += GT) {
+    int row, col, node, plane;
+    ent_unpack(ent[e], row, col, node, plane);
+    A[row * m + col] = ldcg(A + row * m + col) + ccast<double>(lc[plane * len + node]);
+  }
+  cl.sync();
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int cf = F.child[c];
+    if (cf < 0) continue;
+    const FrontD K = fr[cf];
+    const int mc = K.s + K.d;
+    const C* S = scr + fscr[f] + K.fofs;
+    const int* cm = cmap + F.cmap[c];
+    for (int i = gt; i < K.d * K.d; i += GT) {
+      const int a = i / K.d, b = i - a * K.d;
+      const int o = cm[a] * m + cm[b];
+      A[o] = ldcg(A + o) + ldcg(S + (long long)(K.s + a) * mc + K.s + b);
+    }
+    cl.sync();
+  }
+  for (int k = 0; k < s; ++k) {
+    T bv = (T)-1;
+    int bi = k;
+    const int i0 = k + ((q - k % NDC) + NDC) % NDC;
+    for (int i = i0 + tid * NDC; i < s; i += FT * NDC) {
+      const T v = cabs2(ldcg(A + (long long)i * m + k));
+      if (v > bv) { bv = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { redv[warp] = bv; redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < nw; ++w)
+        if (redv[w] > bv || (redv[w] == bv && redi[w] < bi)) { bv = redv[w]; bi = redi[w]; }
+      cand_v = bv;
+      cand_i = bi;
+    }
+    cl.sync();
+    bv = *cl.map_shared_rank(&cand_v, 0);
+    bi = *cl.map_shared_rank(&cand_i, 0);
+    for (int rr = 1; rr < NDC; ++rr) {
+      const T v = *cl.map_shared_rank(&cand_v, rr);
+      const int ii = *cl.map_shared_rank(&cand_i, rr);
+      if (v > bv || (v == bv && ii < bi)) { bv = v; bi = ii; }
+    }
+    const int r = bi;
+    if (tid == 0) {
+      perm[k] = r;
+      if (q == 0 && (!(bv > (T)0) || !(bv < (T)INFINITY))) atomicOr(err, ERRBIT_SINGULAR);
+    }
+    const C pinv = cinv(ldcg(A + (long long)r * m + k));
+    for (int j = tid; j < m; j += FT) {
+      rowk[j] = ldcg(A + (long long)r * m + j) * pinv;
+      rowo[j] = ldcg(A + (long long)k * m + j);
+    }
+    for (int li = tid; q + li * NDC < m; li += FT) {
+      const int i = q + li * NDC;
+      colk[li] = ldcg(A + (long long)(i == k ? r : (i == r ? k : i)) * m + k);
+    }
+    cl.sync();                       // rows k and r are read everywhere before their owners write
+    for (int li = warp; q + li * NDC < m; li += nw) {
+      const int i = q + li * NDC;
+      const C ci = colk[li];
+      C* Ai = A + (long long)i * m;
+      if (i == k) {
+        for (int j = lane; j < m; j += 32) Ai[j] = j == k ? pinv : rowk[j];
+      } else if (i == r) {
+        for (int j = lane; j < m; j += 32) Ai[j] = j == k ? -(ci * pinv) : rowo[j] - ci * rowk[j];
+      } else {
+        for (int j = lane; j < m; j += 32) Ai[j] = j == k ? -(ci * pinv) : ldcg(Ai + j) - ci * rowk[j];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int c = 0; c < s; ++c) colsrc[c] = c;
+    for (int k = s - 1; k >= 0; --k) {
+      const int r = perm[k], t = colsrc[k];
+      colsrc[k] = colsrc[r];
+      colsrc[r] = t;
+    }
+  }
+  cl.sync();                         // every row is final (the Schur block stays in place)
+  C* M = G + ffofs[f] + F.mofs;
+  for (long long i = gt; i < (long long)m * s; i += GT) {
+    const int c = (int)(i / m), row = (int)(i - (long long)c * m);
+    M[i] = ldcg(A + (long long)row * m + colsrc[c]);
+  }
 }
 
 // Forward sweep of one tree height.  CTA = (subdomain, front) x group of NR right-hand sides.
@@ -600,24 +745,45 @@ static cudaError_t nd_factor_t(ddm_ctx* c, const std::vector<int>& reps) {
       used += b;
       ++f1;
     }
+    // per height: fronts that fit in shared memory (one CTA each), then the larger ones (a
+    // cluster each); extra = the shared memory of the single-CTA kernel besides the front
     std::vector<int2> items;
-    std::vector<int> hofs(S->hmax + 2, 0);
-    std::vector<int> hm(S->hmax + 1, 1), hs(S->hmax + 1, 1), hf(S->hmax + 1, 0);
+    std::vector<int> sm0(S->hmax + 1), smn(S->hmax + 1), cl0(S->hmax + 1), cln(S->hmax + 1);
+    std::vector<int> hm(S->hmax + 1, 1), hs(S->hmax + 1, 1), cm(S->hmax + 1, 1), cs(S->hmax + 1, 1);
+    std::vector<long long> fcap(S->hmax + 1, 0);
     for (int h = 0; h <= S->hmax; ++h) {
-      hofs[h] = (int)items.size();
+      // the single-CTA kernel's own shared memory besides the front, for this height's sizes
+      int mh = 1, sh = 1;
       for (size_t f = f0; f < f1; ++f) {
-        const int pl = S->sub_plan[reps[f]];
-        const nd::Plan& P = S->plans[pl];
-        for (int j = 0; j < (int)P.fr.size(); ++j)
-          if (P.fr[j].h == h) {
+        const nd::Plan& P = S->plans[S->sub_plan[reps[f]]];
+        for (const nd::Front& F : P.fr)
+          if (F.h == h) { mh = std::max(mh, F.s + F.d); sh = std::max(sh, F.s); }
+      }
+      const size_t extra = 3 * (size_t)mh * el + 2 * (size_t)sh * sizeof(int) + (nd::FT / 32) * (sizeof(double) + sizeof(int)) + 64;
+      const size_t room = (size_t)optin - 1024 > extra ? (size_t)optin - 1024 - extra : 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        (pass == 0 ? sm0 : cl0)[h] = (int)items.size();
+        for (size_t f = f0; f < f1; ++f) {
+          const int pl = S->sub_plan[reps[f]];
+          const nd::Plan& P = S->plans[pl];
+          for (int j = 0; j < (int)P.fr.size(); ++j) {
+            const nd::Front& F = P.fr[j];
+            if (F.h != h) continue;
+            const int m = F.s + F.d;
+            const bool fits = (size_t)m * m * el <= room;
+            if (fits != (pass == 0)) continue;
             items.push_back(make_int2((int)f, S->front0[pl] + j));
-            const int m = P.fr[j].s + P.fr[j].d;
-            hm[h] = std::max(hm[h], m);
-            hs[h] = std::max(hs[h], P.fr[j].s);
+            if (fits) {
+              hm[h] = std::max(hm[h], m); hs[h] = std::max(hs[h], F.s);
+              fcap[h] = std::max(fcap[h], (long long)m * m);
+            } else {
+              cm[h] = std::max(cm[h], m); cs[h] = std::max(cs[h], F.s);
+            }
           }
+        }
+        (pass == 0 ? smn : cln)[h] = (int)items.size() - (pass == 0 ? sm0 : cl0)[h];
       }
     }
-    hofs[S->hmax + 1] = (int)items.size();
     if (items.size() > S->fitems_cap) {
       dev_free(c, S->d_fitems);
       S->d_fitems = nullptr;
@@ -628,24 +794,25 @@ static cudaError_t nd_factor_t(ddm_ctx* c, const std::vector<int>& reps) {
     if ((e = cudaMemcpyAsync(S->d_fitems, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, c->st)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(S->d_fscr, fscr.data(), sizeof(long long) * reps.size(), cudaMemcpyHostToDevice, c->st)) != cudaSuccess) return e;
     for (int h = 0; h <= S->hmax; ++h) {
-      const int n = hofs[h + 1] - hofs[h];
-      if (n == 0) continue;
-      const size_t extra = 3 * (size_t)hm[h] * el + 2 * (size_t)hs[h] * sizeof(int) + (nd::FT / 32) * (sizeof(double) + sizeof(int)) + 64;
-      const size_t room = (size_t)optin - 1024 > extra ? (size_t)optin - 1024 - extra : 0;
-      // the largest front of this height that fits in shared memory sets the front area
-      long long fcap = 0;
-      for (int q = hofs[h]; q < hofs[h + 1]; ++q) {
-        const nd::Plan& P = S->plans[S->sub_plan[reps[items[q].x]]];
-        const nd::Front& F = P.fr[items[q].y - S->front0[S->sub_plan[reps[items[q].x]]]];
-        const long long mm = (long long)(F.s + F.d) * (F.s + F.d);
-        if ((size_t)mm * el <= room) fcap = std::max(fcap, mm);
+      if (smn[h] > 0) {
+        const size_t smem = (size_t)fcap[h] * el + 3 * (size_t)hm[h] * el + 2 * (size_t)hs[h] * sizeof(int) +
+                            (nd::FT / 32) * (sizeof(double) + sizeof(int)) + 64;
+        ++c->nlaunch;
+        nd::k_nd_factor<TC><<<smn[h], nd::FT, smem, c->st>>>(c->g, S->d_fitems + sm0[h], S->d_fr, S->d_cmap, S->d_ent,
+                                                             c->d_reps, S->d_ffofs, S->d_fscr, (z64*)c->d_G,
+                                                             (z64*)S->d_scr, (int)fcap[h], hm[h], hs[h], c->d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
       }
-      const size_t smem = (size_t)fcap * el + extra;
-      ++c->nlaunch;
-      nd::k_nd_factor<TC><<<n, nd::FT, smem, c->st>>>(c->g, S->d_fitems + hofs[h], S->d_fr, S->d_cmap, S->d_ent, c->d_reps,
-                                                      S->d_ffofs, S->d_fscr, (z64*)c->d_G, (z64*)S->d_scr,
-                                                     (int)fcap, hm[h], hs[h], c->d_err);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (cln[h] > 0) {
+        const size_t smem = (2 * (size_t)cm[h] + (cm[h] + nd::NDC - 1) / nd::NDC) * el + 2 * (size_t)cs[h] * sizeof(int) +
+                            (nd::FT / 32) * (sizeof(double) + sizeof(int)) + 64;
+        if ((e = allow_dynamic_smem((const void*)nd::k_nd_factor_cl<TC>, smem)) != cudaSuccess) return e;
+        ++c->nlaunch;
+        nd::k_nd_factor_cl<TC><<<cln[h] * nd::NDC, nd::FT, smem, c->st>>>(
+            c->g, S->d_fitems + cl0[h], S->d_fr, S->d_cmap, S->d_ent, c->d_reps, S->d_ffofs, S->d_fscr, (z64*)c->d_G,
+            (z64*)S->d_scr, cm[h], cs[h], c->d_err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
     }
     // the host vectors of this chunk are reused by the next one
     if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return e;

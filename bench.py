@@ -627,20 +627,27 @@ def run_table3(args):
     factor): N = 2 .. 64 in mixed precision (complex64 local solves on the tensor cores, FP64
     refinement) and N <= 8 in FP64 (the paper's arithmetic; its step counts are comparable one to
     one).  Table 4 (the seeded layered stand-in, every subdomain its own factor): N <= 16 in mixed
-    precision.  One JSON line with n_DDM_iter, n_DDM_solve = n_iter / (N1 + N2) and the times
-    beside the paper's counts."""
+    precision.  With the nested-dissection (multifrontal) local solver (--local-solver nd or both):
+    FP64 rows for Table 3 (N <= 32) and Table 4 (N <= 8), the paper's arithmetic with its sparse
+    direct local solves.  One JSON line with n_DDM_iter, n_DDM_solve = n_iter / (N1 + N2) and
+    the times beside the paper's counts."""
     import torch
     from paper_1807_04180_gb300 import ddm as D
     with open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")) as fh:
         gold = json.load(fh)
     rows = []
-    plan = [("constant", N, D.DDM_MIXED) for N in args.table3_parts] + \
-           [("constant", N, D.DDM_FP64) for N in args.table3_parts if N <= 8] + \
-           [("layered", N, D.DDM_MIXED) for N in args.table3_parts if N <= 8]
-    for medium, N, prec in plan:
+    plan = []
+    if args.local_solver in ("block", "both"):
+        plan += [("constant", N, D.DDM_MIXED, D.DDM_LOCAL_BLOCK) for N in args.table3_parts] + \
+                [("constant", N, D.DDM_FP64, D.DDM_LOCAL_BLOCK) for N in args.table3_parts if N <= 8] + \
+                [("layered", N, D.DDM_MIXED, D.DDM_LOCAL_BLOCK) for N in args.table3_parts if N <= 8]
+    if args.local_solver in ("nd", "both"):
+        plan += [("constant", N, D.DDM_FP64, D.DDM_LOCAL_ND) for N in args.table3_parts if N <= 32] + \
+                [("layered", N, D.DDM_FP64, D.DDM_LOCAL_ND) for N in args.table3_parts if N <= 8]
+    for medium, N, prec, solver in plan:
         wl = W.paper_table3(N, medium)
         t0 = time.perf_counter()
-        s = D.Solver(wl, precision=prec)
+        s = D.Solver(wl, precision=prec, local_solver=solver)
         torch.cuda.synchronize()
         t_setup = time.perf_counter() - t0
         s.factor()
@@ -651,6 +658,7 @@ def run_table3(args):
         pi = gold[key]["parts"].index(N) if N in gold[key]["parts"] else None
         rows.append({"table": 3 if medium == "constant" else 4, "parts": N, "mesh": wl.n[0],
                      "omega_over_2pi": wl.omega / (2 * math.pi), "precision": "mixed" if prec == D.DDM_MIXED else "fp64",
+                     "local_solver": "nested_dissection" if solver == D.DDM_LOCAL_ND else "block_tridiagonal",
                      "n_ddm_iter": info["ddm_steps"], "n_ddm_solve": info["ddm_steps"] / (2 * N),
                      "paper_n_ddm_iter": gold[key]["n_iter"][pi] if pi is not None else None,
                      "converged": bool(info["converged"]), "rel_residual": info["rel_residual"],
@@ -708,6 +716,8 @@ def main():
     ap.add_argument("--table3", action="store_true",
                     help="the paper's Tables 3-4 at the paper's subdomain size (b = 360), one JSON line")
     ap.add_argument("--table3-parts", type=int, nargs="+", default=[2, 4, 8, 16, 32, 64])
+    ap.add_argument("--local-solver", choices=["block", "nd", "both"], default="both",
+                    help="--table3: block-tridiagonal rows, nested-dissection rows, or both")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--workload", choices=["heterogeneous_2d", "layered_2d_batched", "constant_3d"],

@@ -469,6 +469,12 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
   return DDM_OK;
 }
 
+// The batched local solves of Algorithm 3.1 with the context's local solver.
+static cudaError_t local_solve(ddm_ctx* c, const void* src, void* out, void* accum, int nrhs) {
+  if (c->local_solver == DDM_LOCAL_ND) return nd_solve(c, src, out, accum, nrhs);
+  return launch_local_solve(c, src, out, accum, nrhs);
+}
+
 // =====================================================================================
 // DDM steps (Algorithm 3.1) and the preconditioner
 // =====================================================================================
@@ -486,7 +492,7 @@ static ddm_status run_steps(ddm_ctx* c, const z64* b, int nrhs, int K, z64* w_ou
   for (; s <= K; ++s) {
     {
       TScope ts(c, T_SOLVE);
-      CK(launch_local_solve(c, c->d_src, c->d_ring[s % L], c->d_U, nrhs));
+      CK(local_solve(c, c->d_src, c->d_ring[s % L], c->d_U, nrhs));
     }
     const bool want_res = res_host != nullptr;
     if (s < K || want_res) {
@@ -604,7 +610,7 @@ extern "C" ddm_status ddm_local_solve(ddm_ctx* c, const void* src_dev, void* u_d
   if (!c->factored) return fail(c, DDM_E_STATE, "ddm_factor must run first");
   {
     TScope ts(c, T_SOLVE);
-    CK(launch_local_solve(c, src_dev, u_dev, nullptr, nrhs));
+    CK(local_solve(c, src_dev, u_dev, nullptr, nrhs));
   }
   CK(cudaStreamSynchronize(c->st));
   return check_err_word(c);

@@ -366,7 +366,6 @@ static cudaError_t solve_t(ddm_ctx* c, const void* src, void* out, void* U, int 
 }
 
 cudaError_t launch_local_solve(ddm_ctx* c, const void* src, void* out, void* accum, int nrhs) {
-  if (c->local_solver == DDM_LOCAL_ND) return nd_solve(c, src, out, accum, nrhs);
   if (c->blockpath) return launch_local_solve3d(c, src, out, accum, nrhs);
   return c->prec == DDM_MIXED ? solve_t<float>(c, src, out, accum, nrhs) : solve_t<double>(c, src, out, accum, nrhs);
 }

@@ -191,6 +191,24 @@ ddm_status ddm_set_tensor_cores(ddm_ctx *ctx, int enable);
  * met).                                                                     */
 ddm_status ddm_set_rhs_per_cta(ddm_ctx *ctx, int nr);
 
+/* Pivoting of the dense-block factorisation: 3D partitions, and 2D subdomains
+ * wider than the 2D kernels (see ddm_factor).  Each Schur block D_k is
+ * inverted by Gauss-Jordan in panels of 16 columns (8 in complex128).  With
+ * tau > 0 (the default is 4) a panel's pivots are searched among its own
+ * diagonal rows only.  Every CTA then eliminates the panel without waiting
+ * for the others, instead of taking one cluster-wide search per pivot.  The
+ * choice is checked: if an unpivoted row outside the panel holds more than
+ * tau times its column's pivot (threshold pivoting with u = 1/tau), or a
+ * panel has no usable pivot, ddm_factor redoes the whole factorisation with
+ * partial pivoting over all rows.  The result then equals that of tau = 0,
+ * which always searches all rows.  The Schur blocks of this method contain a
+ * PML layer; partial pivoting over all rows takes their diagonal entries in
+ * practice, so the check rarely fails.  Takes effect at the next ddm_factor.
+ * ddm_pivoting_info returns tau and the number of factorisations redone so
+ * far.  Errors: DDM_E_INVAL (null context, tau outside [0, 1e6]).           */
+ddm_status ddm_set_pivoting(ddm_ctx *ctx, double tau);
+ddm_status ddm_pivoting_info(const ddm_ctx *ctx, double *tau, int64_t *redone);
+
 /* Local solver of Algorithm 3.1's subdomain problems.  The paper factors
  * each subdomain with a sparse direct (multifrontal) solver (Section 4).
  * DDM_LOCAL_BLOCK (the default): the block-tridiagonal LU in explicit-inverse

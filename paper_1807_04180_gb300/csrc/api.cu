@@ -456,7 +456,22 @@ extern "C" ddm_status ddm_factor(ddm_ctx* c) {
       if (c->prec == DDM_MIXED && c->p.max_rhs >= 16) CK(tc2d_pack_factors(c));
     }
     else {
-      CK(launch_factor3d(c, reps));
+      CK(launch_factor3d(c, reps));   // ends with a stream synchronisation
+      if (c->piv_tau > 0) {
+        // pivots were searched among each panel's diagonal rows: redo the factorisation with the
+        // search over all rows if a threshold check failed (or a block had no usable pivot)
+        int h = 0;
+        CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (h & (ERRBIT_WEAKPIV | ERRBIT_SINGULAR)) {
+          CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+          c->piv_full = true;
+          const cudaError_t e = launch_factor3d(c, reps);
+          c->piv_full = false;
+          CK(e);
+          ++c->piv_redone;
+        }
+      }
       if (c->prec == DDM_MIXED) CK(tc3d_pack_factors(c));
     }
   }
@@ -954,6 +969,20 @@ extern "C" ddm_status ddm_set_graph(ddm_ctx* c, int enable) {
                 "graph replay of M_K is implemented for 2D partitions: subdomains at most 128 nodes wide, or the "
                 "nested-dissection local solver");
   c->use_graph = enable != 0;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_set_pivoting(ddm_ctx* c, double tau) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (!(tau >= 0.0) || !(tau <= 1e6)) return fail(c, DDM_E_INVAL, "pivot threshold must be in [0, 1e6]");
+  c->piv_tau = tau;
+  return DDM_OK;
+}
+
+extern "C" ddm_status ddm_pivoting_info(const ddm_ctx* c, double* tau, int64_t* redone) {
+  if (!c) return fail(nullptr, DDM_E_INVAL, "null context");
+  if (tau) *tau = c->piv_tau;
+  if (redone) *redone = c->piv_redone;
   return DDM_OK;
 }
 

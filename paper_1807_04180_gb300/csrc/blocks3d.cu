@@ -145,6 +145,33 @@ template <> struct F3Panel<double> { static constexpr int W = 8; };
 // same barriers (the loop bounds are kernel arguments), so the cluster barriers cannot deadlock.
 constexpr int F3C_N = 8, F3C_T = 256;
 
+// Compose a panel's interchanges (step q moved row perm[q] to row p0 + q) into (destination,
+// source) rows for k_f3_gather: lane t holds one touched row (the panel's rows first) and the row
+// its content comes from.  One warp; swl[0] = number of pairs.
+__device__ __forceinline__ void f3_compose_swaps(int p0, int w, const int* s_perm, int* swl, int lane) {
+  int row_l = lane < w ? p0 + lane : -1, src_l = row_l, n = w;
+  for (int qc = 0; qc < w; ++qc) {
+    const int pr = s_perm[qc];
+    const unsigned m = __ballot_sync(0xffffffffu, row_l == pr);
+    int bb;
+    if (m) {
+      bb = __ffs(m) - 1;
+    } else {
+      bb = n;
+      if (lane == n) { row_l = pr; src_l = pr; }
+      ++n;
+    }
+    const int sa = __shfl_sync(0xffffffffu, src_l, qc), sb = __shfl_sync(0xffffffffu, src_l, bb);
+    if (lane == qc) src_l = sb;
+    if (lane == bb) src_l = sa;
+  }
+  const bool emit = lane < n && (lane < w || src_l != row_l);
+  const unsigned em = __ballot_sync(0xffffffffu, emit);
+  const int pos = __popc(em & ((1u << lane) - 1u));
+  if (emit) { swl[1 + 2 * pos] = row_l; swl[2 + 2 * pos] = src_l; }
+  if (lane == 0) swl[0] = __popc(em);
+}
+
 template <typename T>
 __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
     k_f3_panel_cl(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* swl, int* err) {
@@ -281,31 +308,125 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
   for (int q = 0; q < PW; ++q)
     if (have && q < w) W[(long long)i * ldw + p0 + q] = R[q];
   if (tid == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
-  if (rank == 0 && wid == 0) {
-    // compose the panel's interchanges into (destination, source) rows for k_f3_gather: lane t
-    // holds one touched row (the panel's rows first) and the row its content comes from
-    int row_l = lane < w ? p0 + lane : -1, src_l = row_l, n = w;
-    for (int qc = 0; qc < w; ++qc) {
-      const int pr = s_perm[qc];
-      const unsigned m = __ballot_sync(0xffffffffu, row_l == pr);
-      int bb;
-      if (m) {
-        bb = __ffs(m) - 1;
-      } else {
-        bb = n;
-        if (lane == n) { row_l = pr; src_l = pr; }
-        ++n;
+  if (rank == 0 && wid == 0) f3_compose_swaps(p0, w, s_perm, swl, lane);
+}
+
+// The panel elimination with the pivot search restricted to the panel's diagonal rows
+// [p0, p0 + w): the Schur blocks of this method contain a PML layer, and partial pivoting over
+// all rows takes their diagonal entries (pivot growth 1 in every block examined), so the cluster
+// search above is not needed to find them.  Every CTA's warp 0 runs the w steps on the block rows
+// alone (one row per lane, interchanges inside the block), recording each step's old pivot row
+// and reciprocal; then every thread replays the recorded steps on its own row, in the same
+// arithmetic as k_f3_panel_cl: no barrier between CTAs.  CTA 0 writes the block rows, perm and
+// the interchange list.  Threshold: the search over all rows would pick an unpivoted row i
+// instead whenever |W[i][c]| > |p_c|; the restricted choice is accepted while every such row
+// stays within |W[i][c]| <= tau |p_c| (threshold pivoting with u = 1/tau), else ERRBIT_WEAKPIV
+// is set and the host redoes the factorisation with k_f3_panel_cl.
+constexpr int F3B_T = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(F3B_T) k_f3_panel_blk(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* swl,
+                                                      T tau2, int* err) {
+  constexpr int PW = F3Panel<T>::W;
+  __shared__ cplx<T> s_prow[PW][PW];     // old pivot row of each step
+  __shared__ cplx<T> s_inv[PW];
+  __shared__ cplx<T> s_rowc[PW];         // old row c of the current step
+  __shared__ int s_perm[PW];
+  __shared__ int s_bad, s_weak;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) { s_bad = 0; s_weak = 0; }
+  __syncthreads();
+  if (wid == 0) {
+    const bool hb = lane < w;
+    cplx<T> R[PW];
+#pragma unroll
+    for (int q = 0; q < PW; ++q) R[q] = (hb && q < w) ? W[(long long)(p0 + lane) * ldw + p0 + q] : mk<T>(0, 0);
+#pragma unroll
+    for (int qc = 0; qc < PW; ++qc) {
+      if (qc >= w) break;
+      const cplx<T> x = R[qc];
+      T best = (lane >= qc && hb) ? cabs2(x) : (T)-1;
+      int bi = lane;
+      for (int o = 16; o; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      const int sa = __shfl_sync(0xffffffffu, src_l, qc), sb = __shfl_sync(0xffffffffu, src_l, bb);
-      if (lane == qc) src_l = sb;
-      if (lane == bb) src_l = sa;
+      const bool ok = best > (T)0 && isfinite(best);
+      const int r = ok ? bi : qc;
+      if (lane == r) {
+#pragma unroll
+        for (int q = 0; q < PW; ++q) s_prow[qc][q] = R[q];
+      }
+      if (lane == qc) {
+#pragma unroll
+        for (int q = 0; q < PW; ++q) s_rowc[q] = R[q];
+      }
+      __syncwarp();
+      const cplx<T> inv = ok ? cinv(s_prow[qc][qc]) : mk<T>(0, 0);
+      if (lane == 0) {
+        s_inv[qc] = inv;
+        s_perm[qc] = p0 + r;
+        if (!ok) s_bad = 1;
+      }
+      if (hb) {
+        if (lane == qc) {
+#pragma unroll
+          for (int q = 0; q < PW; ++q) R[q] = q == qc ? inv : s_prow[qc][q] * inv;
+        } else {
+          if (lane == r) {
+#pragma unroll
+            for (int q = 0; q < PW; ++q) R[q] = s_rowc[q];   // row r takes old row c
+          }
+          const cplx<T> fiv = (-R[qc]) * inv;
+#pragma unroll
+          for (int q = 0; q < PW; ++q) {
+            if (q == qc) R[q] = fiv;
+            else cfma(R[q], fiv, s_prow[qc][q]);
+          }
+        }
+      }
+      __syncwarp();
     }
-    const bool emit = lane < n && (lane < w || src_l != row_l);
-    const unsigned em = __ballot_sync(0xffffffffu, emit);
-    const int pos = __popc(em & ((1u << lane) - 1u));
-    if (emit) { swl[1 + 2 * pos] = row_l; swl[2 + 2 * pos] = src_l; }
-    if (lane == 0) swl[0] = __popc(em);
+    if (blockIdx.x == 0) {
+      if (hb) {
+#pragma unroll
+        for (int q = 0; q < PW; ++q)
+          if (q < w) W[(long long)(p0 + lane) * ldw + p0 + q] = R[q];
+      }
+      if (lane < w) perm[p0 + lane] = s_perm[lane];
+      f3_compose_swaps(p0, w, s_perm, swl, lane);
+    }
   }
+  __syncthreads();
+  bool weak = false;
+  for (int i = blockIdx.x * F3B_T + tid; i < b; i += gridDim.x * F3B_T) {
+    if (i >= p0 && i < p0 + w) continue;
+    const bool unpiv = i >= p0 + w;      // rows below p0 are earlier pivot rows
+    cplx<T> R[PW];
+#pragma unroll
+    for (int q = 0; q < PW; ++q) R[q] = q < w ? W[(long long)i * ldw + p0 + q] : mk<T>(0, 0);
+#pragma unroll
+    for (int qc = 0; qc < PW; ++qc) {
+      if (qc >= w) break;
+      const cplx<T> inv = s_inv[qc];
+      const cplx<T> x = R[qc];
+      weak = weak || (unpiv && cabs2(x) > tau2 * cabs2(s_prow[qc][qc]));
+      const cplx<T> fiv = (-x) * inv;
+#pragma unroll
+      for (int q = 0; q < PW; ++q) {
+        if (q == qc) R[q] = fiv;
+        else cfma(R[q], fiv, s_prow[qc][q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PW; ++q)
+      if (q < w) W[(long long)i * ldw + p0 + q] = R[q];
+  }
+  if (weak) s_weak = 1;
+  __syncthreads();
+  if (tid == 0 && blockIdx.x == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
+  if (tid == 0 && s_weak) atomicOr(err, ERRBIT_WEAKPIV);
 }
 
 // thread per column j outside the panel, driven by the list of k_f3_panel_cl: every moved row's
@@ -607,6 +728,14 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   }
   cudaStream_t s2 = side.s;
   cudaEvent_t evA = side.a, evB = side.b;
+  // panel elimination: pivots searched among the panel's diagonal rows (threshold-checked), or
+  // over all rows by the cluster kernel (tau = 0, or when a factorisation is redone)
+  const bool full = c->piv_tau <= 0 || c->piv_full;
+  const T tau2 = (T)(c->piv_tau * c->piv_tau);
+  auto panel = [&](int bb, int p, int wp) {
+    if (full) k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(bb, p, wp, W, ldw, perm, swl, c->d_err);
+    else k_f3_panel_blk<T><<<(bb + F3B_T - 1) / F3B_T, F3B_T, 0, c->st>>>(bb, p, wp, W, ldw, perm, swl, tau2, c->d_err);
+  };
   cplx<T>* G = (cplx<T>*)c->d_G;
   for (size_t f = 0; f < reps.size(); ++f) {
     const int b = c->fac_b[f], m = c->fac_m[f], ldb = c->fac_ldb[f];
@@ -621,7 +750,7 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
         // gather waits for that update (it moves rows in all columns and rewrites Tp).
         const dim3 gr((b + 63) / 64, (b + 63) / 64);
         ++c->nlaunch;
-        k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, 0, std::min(PW, b), W, ldw, perm, swl, c->d_err);
+        panel(b, 0, std::min(PW, b));
         for (int p0 = 0; p0 < b; p0 += PW) {
           const int w = std::min(PW, b - p0);
           const int p1 = p0 + w, w1 = p1 < b ? std::min(PW, b - p1) : 0;
@@ -632,7 +761,7 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
           if (w1 > 0) {
             c->nlaunch += 2;
             k_f3_rankw_cols<T><<<(b * w1 + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp, p1, w1);
-            k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(b, p1, w1, W, ldw, perm, swl, c->d_err);
+            panel(b, p1, w1);
           }
           if ((e = cudaStreamWaitEvent(s2, evA, 0)) != cudaSuccess) break;
           if (rw_tc) {

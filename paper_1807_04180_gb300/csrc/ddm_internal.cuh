@@ -106,7 +106,9 @@ struct Geom {
 };
 
 // error word bits set by kernels
-enum { ERRBIT_TIMEOUT = 1, ERRBIT_SINGULAR = 2, ERRBIT_NONFINITE = 4 };
+// ERRBIT_WEAKPIV: a dense-block factorisation with pivots restricted to each panel's diagonal rows
+// failed its threshold check (not an error: it is redone with the search over all rows)
+enum { ERRBIT_TIMEOUT = 1, ERRBIT_SINGULAR = 2, ERRBIT_NONFINITE = 4, ERRBIT_WEAKPIV = 8 };
 
 // ---------------------------------------------------------------------------
 // operator coefficients at a node (computed in FP64 from the alpha tables)
@@ -266,6 +268,12 @@ struct ddm_ctx {
   int* d_fsel = nullptr;                  // nsub: factor ids in launch order (by kernel variant)
   ddm::z64* d_coef = nullptr;             // (kry_m + 1) x kry_nb Gram-Schmidt coefficients
   // local solver (ddm_set_local_solver) and the nested-dissection plans, work lists and buffers
+  // pivoting of the dense-block factorisation (3D and wide 2D; ddm_set_pivoting): threshold tau
+  // of the search restricted to each panel's diagonal rows (0: the cluster search over all rows);
+  // piv_full is set while a factorisation is redone after a failed check, piv_redone counts them
+  double piv_tau = 4.0;
+  bool piv_full = false;
+  long long piv_redone = 0;
   int local_solver = DDM_LOCAL_BLOCK;
   int nd_leaf = DDM_ND_LEAF_DEFAULT;
   ddm::nd::State* nd = nullptr;

@@ -104,6 +104,8 @@ def lib() -> ctypes.CDLL:
         "ddm_set_tensor_cores": [_P, ctypes.c_int],
         "ddm_set_rhs_per_cta": [_P, ctypes.c_int],
         "ddm_set_local_solver": [_P, ctypes.c_int, ctypes.c_int],
+        "ddm_set_pivoting": [_P, ctypes.c_double],
+        "ddm_pivoting_info": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "ddm_nd_plan": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ddm_nd_plan_info), _P, _P, _P, _P,
                         _P],
         "ddm_autotune_log": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -201,6 +203,18 @@ def ddm_set_rhs_per_cta(ctx, nr: int = 0) -> None:
 
 def ddm_set_local_solver(ctx, solver: int = DDM_LOCAL_BLOCK, leaf: int = 0) -> None:
     _check(lib().ddm_set_local_solver(ctx, int(solver), int(leaf)), ctx)
+
+
+def ddm_set_pivoting(ctx, tau: float = 4.0) -> None:
+    _check(lib().ddm_set_pivoting(ctx, float(tau)), ctx)
+
+
+def ddm_pivoting_info(ctx):
+    """(tau, number of factorisations redone with the search over all rows)"""
+    t = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().ddm_pivoting_info(ctx, ctypes.byref(t), ctypes.byref(n)), ctx)
+    return t.value, n.value
 
 
 def ddm_nd_plan(nx: int, ny: int, leaf: int = 0) -> dict:

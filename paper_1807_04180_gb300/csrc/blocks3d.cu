@@ -311,119 +311,91 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
   if (rank == 0 && wid == 0) f3_compose_swaps(p0, w, s_perm, swl, lane);
 }
 
-// The panel elimination with the pivot search restricted to the panel's diagonal rows
-// [p0, p0 + w): the Schur blocks of this method contain a PML layer, and partial pivoting over
-// all rows takes their diagonal entries (pivot growth 1 in every block examined), so the cluster
-// search above is not needed to find them.  Every CTA's warp 0 runs the w steps on the block rows
-// alone (one row per lane, interchanges inside the block), recording each step's old pivot row
-// and reciprocal; then every thread replays the recorded steps on its own row, in the same
-// arithmetic as k_f3_panel_cl: no barrier between CTAs.  CTA 0 writes the block rows, perm and
-// the interchange list.  Threshold: the search over all rows would pick an unpivoted row i
-// instead whenever |W[i][c]| > |p_c|; the restricted choice is accepted while every such row
-// stays within |W[i][c]| <= tau |p_c| (threshold pivoting with u = 1/tau), else ERRBIT_WEAKPIV
-// is set and the host redoes the factorisation with k_f3_panel_cl.
-constexpr int F3B_T = 128;
+// The panel elimination with the pivots taken on the panel's diagonal (no interchanges), checked.
+// The Schur blocks of this method contain a PML layer, and partial pivoting over all rows takes
+// their diagonal entries (pivot growth 1 in every block examined), so the cluster search above is
+// not needed to find them.  Without interchanges, Gauss-Jordan on the panel turns its diagonal
+// block A into A^-1 and every other row's panel values v into X = -v A^-1 (rows of earlier panels
+// included).  Each CTA therefore inverts A in shared memory (one element per thread, two barriers
+// per step, no barrier between CTAs) and forms X for its rows as one 1 x w by w x w product; CTA 0
+// writes A^-1, the identity permutation and the interchange list.  Checks, against threshold tau:
+// a block row below the step's pivot holding more than tau times it (what partial pivoting would
+// have swapped in), or an unpivoted row's multiplier |X| above tau, sets ERRBIT_WEAKPIV and the
+// host redoes the factorisation with k_f3_panel_cl.
+constexpr int F3B_T = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(F3B_T) k_f3_panel_blk(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* swl,
                                                       T tau2, int* err) {
   constexpr int PW = F3Panel<T>::W;
-  __shared__ cplx<T> s_prow[PW][PW];     // old pivot row of each step
-  __shared__ cplx<T> s_inv[PW];
-  __shared__ cplx<T> s_rowc[PW];         // old row c of the current step
+  __shared__ cplx<T> As[PW][PW + 1];
   __shared__ int s_perm[PW];
   __shared__ int s_bad, s_weak;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int ea = tid / PW, eq = tid - ea * PW;             // this thread's element of the block
+  const bool he = ea < w && eq < w;
   if (tid == 0) { s_bad = 0; s_weak = 0; }
+  if (he) As[ea][eq] = W[(long long)(p0 + ea) * ldw + p0 + eq];
   __syncthreads();
-  if (wid == 0) {
-    const bool hb = lane < w;
-    cplx<T> R[PW];
-#pragma unroll
-    for (int q = 0; q < PW; ++q) R[q] = (hb && q < w) ? W[(long long)(p0 + lane) * ldw + p0 + q] : mk<T>(0, 0);
-#pragma unroll
-    for (int qc = 0; qc < PW; ++qc) {
-      if (qc >= w) break;
-      const cplx<T> x = R[qc];
-      T best = (lane >= qc && hb) ? cabs2(x) : (T)-1;
-      int bi = lane;
-      for (int o = 16; o; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      const bool ok = best > (T)0 && isfinite(best);
-      const int r = ok ? bi : qc;
-      if (lane == r) {
-#pragma unroll
-        for (int q = 0; q < PW; ++q) s_prow[qc][q] = R[q];
-      }
-      if (lane == qc) {
-#pragma unroll
-        for (int q = 0; q < PW; ++q) s_rowc[q] = R[q];
-      }
-      __syncwarp();
-      const cplx<T> inv = ok ? cinv(s_prow[qc][qc]) : mk<T>(0, 0);
-      if (lane == 0) {
-        s_inv[qc] = inv;
-        s_perm[qc] = p0 + r;
-        if (!ok) s_bad = 1;
-      }
-      if (hb) {
-        if (lane == qc) {
-#pragma unroll
-          for (int q = 0; q < PW; ++q) R[q] = q == qc ? inv : s_prow[qc][q] * inv;
+  bool weak = false, bad = false;
+  for (int qc = 0; qc < w; ++qc) {
+    const cplx<T> pv = As[qc][qc];
+    const T pa = cabs2(pv);
+    const bool ok = pa > (T)0 && isfinite(pa);
+    bad = bad || !ok;
+    const cplx<T> inv = ok ? cinv(pv) : mk<T>(0, 0);
+    cplx<T> colv = mk<T>(0, 0), rowv = mk<T>(0, 0), cur = mk<T>(0, 0);
+    if (he) { colv = As[ea][qc]; rowv = As[qc][eq]; cur = As[ea][eq]; }
+    __syncthreads();
+    if (he) {
+      cplx<T> nv;
+      if (ea == qc) {
+        nv = eq == qc ? inv : rowv * inv;
+      } else {
+        const cplx<T> fiv = (-colv) * inv;
+        if (eq == qc) {
+          nv = fiv;
+          weak = weak || (ea > qc && cabs2(colv) > tau2 * pa);
         } else {
-          if (lane == r) {
-#pragma unroll
-            for (int q = 0; q < PW; ++q) R[q] = s_rowc[q];   // row r takes old row c
-          }
-          const cplx<T> fiv = (-R[qc]) * inv;
-#pragma unroll
-          for (int q = 0; q < PW; ++q) {
-            if (q == qc) R[q] = fiv;
-            else cfma(R[q], fiv, s_prow[qc][q]);
-          }
+          nv = cur;
+          cfma(nv, fiv, rowv);
         }
       }
-      __syncwarp();
+      As[ea][eq] = nv;
     }
-    if (blockIdx.x == 0) {
-      if (hb) {
-#pragma unroll
-        for (int q = 0; q < PW; ++q)
-          if (q < w) W[(long long)(p0 + lane) * ldw + p0 + q] = R[q];
-      }
-      if (lane < w) perm[p0 + lane] = s_perm[lane];
-      f3_compose_swaps(p0, w, s_perm, swl, lane);
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  bool weak = false;
+  if (blockIdx.x == 0) {
+    if (he) W[(long long)(p0 + ea) * ldw + p0 + eq] = As[ea][eq];
+    if (tid < w) { s_perm[tid] = p0 + tid; perm[p0 + tid] = p0 + tid; }
+    __syncthreads();
+    if (wid == 0) f3_compose_swaps(p0, w, s_perm, swl, lane);
+  }
   for (int i = blockIdx.x * F3B_T + tid; i < b; i += gridDim.x * F3B_T) {
     if (i >= p0 && i < p0 + w) continue;
     const bool unpiv = i >= p0 + w;      // rows below p0 are earlier pivot rows
-    cplx<T> R[PW];
+    cplx<T> v[PW], x[PW];
 #pragma unroll
-    for (int q = 0; q < PW; ++q) R[q] = q < w ? W[(long long)i * ldw + p0 + q] : mk<T>(0, 0);
+    for (int q = 0; q < PW; ++q) {
+      v[q] = q < w ? W[(long long)i * ldw + p0 + q] : mk<T>(0, 0);
+      x[q] = mk<T>(0, 0);
+    }
 #pragma unroll
-    for (int qc = 0; qc < PW; ++qc) {
-      if (qc >= w) break;
-      const cplx<T> inv = s_inv[qc];
-      const cplx<T> x = R[qc];
-      weak = weak || (unpiv && cabs2(x) > tau2 * cabs2(s_prow[qc][qc]));
-      const cplx<T> fiv = (-x) * inv;
+    for (int a2 = 0; a2 < PW; ++a2) {
+      if (a2 >= w) break;
+      const cplx<T> nv = -v[a2];
 #pragma unroll
-      for (int q = 0; q < PW; ++q) {
-        if (q == qc) R[q] = fiv;
-        else cfma(R[q], fiv, s_prow[qc][q]);
-      }
+      for (int q = 0; q < PW; ++q) cfma(x[q], nv, As[a2][q]);
     }
 #pragma unroll
     for (int q = 0; q < PW; ++q)
-      if (q < w) W[(long long)i * ldw + p0 + q] = R[q];
+      if (q < w) {
+        weak = weak || (unpiv && cabs2(x[q]) > tau2);
+        W[(long long)i * ldw + p0 + q] = x[q];
+      }
   }
   if (weak) s_weak = 1;
+  if (bad) s_bad = 1;
   __syncthreads();
   if (tid == 0 && blockIdx.x == 0 && s_bad) atomicOr(err, ERRBIT_SINGULAR);
   if (tid == 0 && s_weak) atomicOr(err, ERRBIT_WEAKPIV);

@@ -321,21 +321,34 @@ __global__ void __cluster_dims__(F3C_N, 1, 1) __launch_bounds__(F3C_T)
 // writes A^-1, the identity permutation and the interchange list.  Checks, against threshold tau:
 // a block row below the step's pivot holding more than tau times it (what partial pivoting would
 // have swapped in), or an unpivoted row's multiplier |X| above tau, sets ERRBIT_WEAKPIV and the
-// host redoes the factorisation with k_f3_panel_cl.
+// host redoes the factorisation with k_f3_panel_cl.  With wp > 0 the kernel first applies the
+// previous panel [pp, pp + wp) to this panel's columns, W[i][j] += sum_q W[i][pp + q] Tp[q][j]
+// (what k_f3_rankw_cols does), so that update is not a launch of its own on the critical path.
 constexpr int F3B_T = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(F3B_T) k_f3_panel_blk(int b, int p0, int w, cplx<T>* W, int ldw, int* perm, int* swl,
-                                                      T tau2, int* err) {
+__global__ void __launch_bounds__(F3B_T) k_f3_panel_blk(int b, int pp, int wp, const cplx<T>* __restrict__ Tp, int p0,
+                                                      int w, cplx<T>* W, int ldw, int* perm, int* swl, T tau2,
+                                                      int* err) {
   constexpr int PW = F3Panel<T>::W;
   __shared__ cplx<T> As[PW][PW + 1];
+  __shared__ cplx<T> Ts[PW][PW];         // the previous panel's old pivot rows in this panel's columns
   __shared__ int s_perm[PW];
   __shared__ int s_bad, s_weak;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int ea = tid / PW, eq = tid - ea * PW;             // this thread's element of the block
   const bool he = ea < w && eq < w;
   if (tid == 0) { s_bad = 0; s_weak = 0; }
-  if (he) As[ea][eq] = W[(long long)(p0 + ea) * ldw + p0 + eq];
+  if (tid < wp * w) {
+    const int q = tid / w, j = tid - q * w;
+    Ts[q][j] = Tp[(long long)q * ldw + p0 + j];
+  }
+  __syncthreads();
+  if (he) {
+    cplx<T> v = W[(long long)(p0 + ea) * ldw + p0 + eq];
+    for (int q = 0; q < wp; ++q) cfma(v, W[(long long)(p0 + ea) * ldw + pp + q], Ts[q][eq]);
+    As[ea][eq] = v;
+  }
   __syncthreads();
   bool weak = false, bad = false;
   for (int qc = 0; qc < w; ++qc) {
@@ -379,6 +392,15 @@ __global__ void __launch_bounds__(F3B_T) k_f3_panel_blk(int b, int p0, int w, cp
     for (int q = 0; q < PW; ++q) {
       v[q] = q < w ? W[(long long)i * ldw + p0 + q] : mk<T>(0, 0);
       x[q] = mk<T>(0, 0);
+    }
+    if (wp > 0) {                        // the previous panel's update of these columns
+#pragma unroll
+      for (int q2 = 0; q2 < PW; ++q2) {
+        if (q2 >= wp) break;
+        const cplx<T> xp = W[(long long)i * ldw + pp + q2];
+#pragma unroll
+        for (int q = 0; q < PW; ++q) cfma(v[q], xp, Ts[q2][q]);
+      }
     }
 #pragma unroll
     for (int a2 = 0; a2 < PW; ++a2) {
@@ -704,9 +726,13 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
   // over all rows by the cluster kernel (tau = 0, or when a factorisation is redone)
   const bool full = c->piv_tau <= 0 || c->piv_full;
   const T tau2 = (T)(c->piv_tau * c->piv_tau);
-  auto panel = [&](int bb, int p, int wp) {
-    if (full) k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(bb, p, wp, W, ldw, perm, swl, c->d_err);
-    else k_f3_panel_blk<T><<<(bb + F3B_T - 1) / F3B_T, F3B_T, 0, c->st>>>(bb, p, wp, W, ldw, perm, swl, tau2, c->d_err);
+  // panel [p, p + wn); with the restricted kernel the previous panel [pp, pp + wpp)'s update of its
+  // columns is fused in (wpp = 0: none)
+  auto panel = [&](int bb, int pp, int wpp, int p, int wn) {
+    if (full) k_f3_panel_cl<T><<<F3C_N, F3C_T, 0, c->st>>>(bb, p, wn, W, ldw, perm, swl, c->d_err);
+    else
+      k_f3_panel_blk<T><<<(bb + F3B_T - 1) / F3B_T, F3B_T, 0, c->st>>>(bb, pp, wpp, Tp, p, wn, W, ldw, perm, swl, tau2,
+                                                                      c->d_err);
   };
   cplx<T>* G = (cplx<T>*)c->d_G;
   for (size_t f = 0; f < reps.size(); ++f) {
@@ -722,7 +748,7 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
         // gather waits for that update (it moves rows in all columns and rewrites Tp).
         const dim3 gr((b + 63) / 64, (b + 63) / 64);
         ++c->nlaunch;
-        panel(b, 0, std::min(PW, b));
+        panel(b, 0, 0, 0, std::min(PW, b));
         for (int p0 = 0; p0 < b; p0 += PW) {
           const int w = std::min(PW, b - p0);
           const int p1 = p0 + w, w1 = p1 < b ? std::min(PW, b - p1) : 0;
@@ -731,9 +757,14 @@ static cudaError_t factor3d_t(ddm_ctx* c, const std::vector<int>& reps) {
           k_f3_gather<T><<<(b + 127) / 128, 128, 0, c->st>>>(b, p0, w, W, ldw, swl, Tp);
           if ((e = cudaEventRecord(evA, c->st)) != cudaSuccess) break;
           if (w1 > 0) {
-            c->nlaunch += 2;
-            k_f3_rankw_cols<T><<<(b * w1 + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp, p1, w1);
-            panel(b, p1, w1);
+            if (full) {
+              c->nlaunch += 2;
+              k_f3_rankw_cols<T><<<(b * w1 + 255) / 256, 256, 0, c->st>>>(b, p0, w, W, ldw, Tp, p1, w1);
+              panel(b, 0, 0, p1, w1);
+            } else {
+              ++c->nlaunch;
+              panel(b, p0, w, p1, w1);
+            }
           }
           if ((e = cudaStreamWaitEvent(s2, evA, 0)) != cudaSuccess) break;
           if (rw_tc) {

@@ -83,6 +83,9 @@ struct RingPtrs { const void* p[3]; int res_slot[3]; };
 template <typename T>
 struct CoefT { cplx<T> c, m[3], p[3]; };
 
+// the fields of a sender that the transfer reads, staged in shared memory per receiver
+struct NbrS { int lo[3], ext[3], nown[3], pad; long long vofs; };
+
 // Each thread takes one strip node of R and TR_RG right-hand sides (blockIdx.z = group): the
 // stencil terms of -A_R (beta_d .) at the node (sender index, coefficient x cut-off) are built
 // once per direction and applied to every right-hand side of the group.  TR_RG = 1 for a single
@@ -98,7 +101,19 @@ __global__ void __launch_bounds__(128, TR_RG == 1 ? 6 : 5) k_transfer(Geom g, Ri
   const int e = g.e, ov = g.ov, dim = g.dim;
   __shared__ T beta_s[32];
   __shared__ double sh[TR_RG][4];
+  __shared__ NbrS nb_s[NDIR];            // the receiver's neighbours, by direction code
   if (threadIdx.x <= ov && threadIdx.x < 32) beta_s[threadIdx.x] = (T)g.beta[threadIdx.x];
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + NDIR) {
+    const int code = threadIdx.x - 32, id = R.nbr[code];
+    if (id >= 0) {
+      const SubDesc& S = g.subs[id];
+      NbrS v;
+      for (int a = 0; a < 3; ++a) { v.lo[a] = S.lo[a]; v.ext[a] = S.ext[a]; v.nown[a] = S.nown[a]; }
+      v.pad = 0;
+      v.vofs = S.vofs;
+      nb_s[code] = v;
+    }
+  }
   __syncthreads();
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   double res2[TR_RG];
@@ -126,7 +141,7 @@ __global__ void __launch_bounds__(128, TR_RG == 1 ? 6 : 5) k_transfer(Geom g, Ri
       dm &= dm - 1;
       const int d[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
       const int lagd = (d[0] != 0) + (d[1] != 0) + (d[2] != 0);
-      const SubDesc& S = g.subs[R.nbr[code]];
+      const NbrS& S = nb_s[code];
       // the stencil of x in S-local coordinates and the sender's cut-off there (1D factors)
       int y0[3];
       for (int a = 0; a < 3; ++a) y0[a] = x[a] + R.lo[a] - S.lo[a];
@@ -191,7 +206,7 @@ __global__ void __launch_bounds__(128, TR_RG == 1 ? 6 : 5) k_transfer(Geom g, Ri
 #pragma unroll
         for (int rr = 0; rr < TR_RG; ++rr) {
           if (rr >= nr) break;
-          const cplx<T>* u = ub + lvofs(S, r0 + rr, nrhs);
+          const cplx<T>* u = ub + S.vofs * nrhs + (long long)(r0 + rr) * ((long long)S.ext[0] * S.ext[1] * S.ext[2]);
           // -(A_R (beta_d u_S))(x)
           cplx<T> acc = mk<T>(0, 0);
 #pragma unroll
